@@ -1,0 +1,134 @@
+/*
+ * tdgrav: in-plane self-gravity of an infinitesimally thin disk on a uniform grid, by the
+ * B-spline direct method of Wang, Shiue, Wu & Yen (arXiv 1904.07400), on one GB300.
+ *
+ * What a solve computes (paper Eqs. eqnSigma, eqnF, eqnw, eqnwB):
+ *   C          = B-spline coefficients of sigma at order k (Sec. 2.3: C = sigma for k = 1, 2;
+ *                two truncated tridiagonal solves, Eqs. z_system and C_system, for k = 3)
+ *   F^x_ij     = G * sum_{i'j'} C_{i'j'} w^x(i - i', j - j')
+ *   F^y_ij     = G * sum_{i'j'} C_{i'j'} w^y(i - i', j - j')
+ *   w^x(m, n)  = PV int int u (u^2+v^2)^(-3/2) b_k(u/dx + m) b_k(v/dy + n) du dv
+ * with b_k the centred cardinal B-spline of order k on the cell (Sec. 2.3: every spline is
+ * centred on its cell centre).  The convolution is evaluated exactly (up to rounding) by
+ * FFTs on a zero-padded grid (Sec. 4.1: one forward transform of C, two inverse transforms),
+ * so no boundary values are needed for an isolated disk.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are C-contiguous with shape (nx, ny): element [i * ny + j] is cell (x_i, y_j),
+ *     axis 0 is x.  sigma, F^x, F^y, and the adjoint buffers use this layout.
+ *   - Element type follows the plan's precision: double for TDG_FP64, float for TDG_FP32
+ *     and TDG_FP32_TC16.
+ *   - Data pointers are DEVICE pointers on the plan's device, owned by the caller, 16-byte
+ *     aligned.  The library never frees them and keeps no reference after a call returns.
+ *   - Plans own their kernel spectra, twiddle tables and (unless set with
+ *     tdg_set_workspace) their workspace; tdg_destroy frees them.
+ *   - Every call returns a tdg_status; nothing throws across this interface.  Launches are
+ *     asynchronous on the given stream and the solve entry points do not synchronise the
+ *     host; NaN or Inf in the input propagates and is not checked.
+ *   - `stream` is a cudaStream_t (0 = the legacy default stream).
+ */
+#ifndef TDGRAV_H
+#define TDGRAV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDG_OK = 0,
+    TDG_ERR_INVALID_ARG = 1,   /* bad size, order, spacing, null or misaligned pointer   */
+    TDG_ERR_UNSUPPORTED = 2,   /* size beyond the supported transform lengths            */
+    TDG_ERR_NOT_BUILT = 3,     /* solve before tdg_build_kernel_tables                   */
+    TDG_ERR_OOM = 4,           /* device allocation failed                               */
+    TDG_ERR_CUDA = 5,          /* a CUDA runtime call failed                             */
+    TDG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (batched launch)    */
+    TDG_ERR_DEVICE_BOUNDS = 7  /* a device-side index check failed (checked builds)      */
+} tdg_status;
+
+typedef enum {
+    TDG_FP64 = 0,       /* every step in double                                          */
+    TDG_FP32 = 1,       /* float transforms, spectra rounded from the FP64 build         */
+    TDG_FP32_TC16 = 2   /* float, radix-16 DFT stages as split FP16 hi/lo tensor-core
+                           products accumulated in FP32                                  */
+} tdg_precision;
+
+typedef struct tdg_plan_s* tdg_plan;
+typedef struct CUstream_st* tdg_stream;
+
+/* Create a plan for an nx x ny grid of cells dx x dy, B-spline order 1..3, constant G.
+ * Allocates nothing on the device yet.  Errors: INVALID_ARG for order not in {1,2,3},
+ * nx or ny < 1, dx or dy not finite and > 0, G not finite, out == NULL; UNSUPPORTED for
+ * nx or ny > 4096; CUDA if `device` cannot be selected. */
+tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double dy,
+                    double G, tdg_precision prec, int device);
+
+/* Build the kernel tables w^x, w^y for all offsets |m| < nx, |n| < ny in FP64 on the
+ * device (Sec. 2.1-2.2), place them on the periodic padded grid and transform them into
+ * the two kernel spectra, rounded to the plan's precision.  Done once per plan (Sec. 4.2:
+ * the kernel integrals are computed once and reused).  Synchronises `stream` before
+ * returning (the FP64 temporaries are freed).  Errors: OOM, CUDA. */
+tdg_status tdg_build_kernel_tables(tdg_plan p, tdg_stream stream);
+
+/* Bytes of device workspace a solve or adjoint of this plan needs. */
+size_t tdg_workspace_bytes(const tdg_plan p);
+
+/* Hand the plan a caller-owned workspace of at least tdg_workspace_bytes(p) bytes,
+ * 256-byte aligned; the plan then allocates none of its own.  ptr == NULL returns to
+ * plan-owned workspace (allocated at the next solve).  Errors: INVALID_ARG. */
+tdg_status tdg_set_workspace(tdg_plan p, void* ptr, size_t bytes);
+
+/* sigma -> (F^x, F^y) (Eq. eqnF).  sigma, fx, fy: nx*ny elements each.  fx and fy must
+ * not alias sigma or each other.  Errors: INVALID_ARG (null/misaligned), NOT_BUILT, OOM
+ * (first call allocates the workspace if none was set), CUDA. */
+tdg_status tdg_solve_forces(tdg_plan p, const void* sigma, void* fx, void* fy,
+                            tdg_stream stream);
+
+/* `count` independent solves, each with its own plan (any nx, ny, order; all plans must
+ * share one precision and device), executed by one persistent launch that walks a work
+ * list of (grid, pass, tile) items in pass order.  sigma[d], fx[d], fy[d] follow the
+ * layout of tdg_solve_forces for plans[d].  Errors: as tdg_solve_forces, INVALID_ARG for
+ * mixed precisions/devices; a device-side dependency wait that exceeds its bound sets the
+ * error word read by tdg_get_device_error (TIMEOUT) instead of hanging. */
+tdg_status tdg_solve_forces_batched(const tdg_plan* plans, int count,
+                                    const void* const* sigma, void* const* fx,
+                                    void* const* fy, tdg_stream stream);
+
+/* Adjoint of tdg_solve_forces: for L = sum(gfx * F^x + gfy * F^y), write
+ * gsigma = dL/dsigma = (B-spline solve)^T (correlation of gfx, gfy with the same kernel
+ * spectra).  All buffers nx*ny elements.  Errors: as tdg_solve_forces. */
+tdg_status tdg_solve_adjoint(tdg_plan p, const void* gfx, const void* gfy, void* gsigma,
+                             tdg_stream stream);
+
+/* Read and clear the plan's device error word (synchronises the plan's device).
+ * TDG_OK if no device-side check failed since the last call. */
+tdg_status tdg_get_device_error(tdg_plan p);
+
+/* Copy the FP64 kernel tables for offsets 0 <= m < nx, 0 <= n < ny (the quadrant that
+ * fixes the others by symmetry: w^x odd in m and even in n, w^y even in m and odd in n)
+ * into host arrays wx, wy of nx*ny doubles each, row-major [m * ny + n].  Only valid
+ * after tdg_build_kernel_tables.  Errors: NOT_BUILT, INVALID_ARG, CUDA. */
+tdg_status tdg_copy_kernel_tables(const tdg_plan p, double* wx, double* wy);
+
+/* Evaluate one kernel-table entry w^x(m, n) (component 0) or w^y(m, n) (component 1) on
+ * the HOST with the same FP64 code the device build runs.  For tests without a GPU.
+ * Errors: INVALID_ARG for bad order/spacing/component or out == NULL. */
+tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy,
+                                 int component, double* out);
+
+/* Transform lengths chosen for the plan: the padded periods px, py (even, 2^a 3^b,
+ * >= 2n - 1) along x and y.  Any out pointer may be NULL. */
+tdg_status tdg_plan_info(const tdg_plan p, int* px, int* py, int* order, int* precision);
+
+/* Release everything the plan owns (synchronises its device first). */
+tdg_status tdg_destroy(tdg_plan p);
+
+/* Static string naming a status code. */
+const char* tdg_status_string(tdg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDGRAV_H */

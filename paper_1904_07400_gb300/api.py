@@ -1,0 +1,159 @@
+"""PyTorch-facing API of tdgrav: plans over torch device memory and streams.
+
+    plan = Plan(nx, ny, order, dx, dy, G=1.0, precision="fp32")
+    fx, fy = plan.forces(sigma)              # sigma: (nx, ny) CUDA tensor
+    gs = plan.adjoint(gx, gy)                # dL/dsigma for L = sum(gx Fx + gy Fy)
+    fx, fy = ThinDiskForces.apply(plan, sigma)   # autograd through the hand-written adjoint
+
+Torch provides the device memory and the current stream; every step of the solve runs in
+the library's CUDA kernels through the C ABI (paper_1904_07400_gb300.native).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import native
+
+_DTYPES = {"fp64": torch.float64, "fp32": torch.float32, "fp32_tc16": torch.float32}
+
+
+def _stream_handle(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+class Plan:
+    """One grid (nx x ny cells of dx x dy), B-spline order 1..3, precision form."""
+
+    def __init__(self, nx: int, ny: int, order: int, dx: float, dy: float, G: float = 1.0,
+                 precision: str = "fp32", device: int | torch.device = 0, build: bool = True):
+        if precision not in native.PRECISION:
+            raise ValueError(f"precision must be one of {sorted(native.PRECISION)}")
+        dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.nx, self.ny, self.order = nx, ny, order
+        self.dx, self.dy, self.G = dx, dy, G
+        self.precision = precision
+        self.dtype = _DTYPES[precision]
+        self.device = dev
+        h = ctypes.c_void_p()
+        native.call("tdg_init", ctypes.byref(h), nx, ny, order, dx, dy, G,
+                    native.PRECISION[precision], dev.index)
+        self._h = h
+        self._built = False
+        if build:
+            self.build()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def build(self) -> None:
+        with torch.cuda.device(self.device):
+            native.call("tdg_build_kernel_tables", self._h, _stream_handle(self.device))
+        self._built = True
+
+    def info(self) -> dict:
+        px, py, order, prec = (ctypes.c_int() for _ in range(4))
+        native.call("tdg_plan_info", self._h, ctypes.byref(px), ctypes.byref(py), ctypes.byref(order),
+                    ctypes.byref(prec))
+        return {"px": px.value, "py": py.value, "order": order.value, "precision": prec.value}
+
+    def workspace_bytes(self) -> int:
+        return int(native.load().tdg_workspace_bytes(self._h))
+
+    def set_workspace(self, buf: torch.Tensor | None) -> None:
+        if buf is None:
+            native.call("tdg_set_workspace", self._h, None, 0)
+        else:
+            native.call("tdg_set_workspace", self._h, _ptr(buf), buf.numel() * buf.element_size())
+        self._ws = buf
+
+    def _check(self, t: torch.Tensor, name: str) -> None:
+        if t.device != self.device or t.dtype != self.dtype or tuple(t.shape) != (self.nx, self.ny) \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape "
+                             f"({self.nx}, {self.ny}) on {self.device}")
+
+    def forces(self, sigma: torch.Tensor, out: tuple | None = None):
+        self._check(sigma, "sigma")
+        if out is None:
+            fx = torch.empty_like(sigma)
+            fy = torch.empty_like(sigma)
+        else:
+            fx, fy = out
+            self._check(fx, "fx")
+            self._check(fy, "fy")
+        native.call("tdg_solve_forces", self._h, _ptr(sigma), _ptr(fx), _ptr(fy), _stream_handle(self.device))
+        return fx, fy
+
+    def adjoint(self, gx: torch.Tensor, gy: torch.Tensor, out: torch.Tensor | None = None):
+        self._check(gx, "gx")
+        self._check(gy, "gy")
+        gs = torch.empty_like(gx) if out is None else out
+        self._check(gs, "gsigma")
+        native.call("tdg_solve_adjoint", self._h, _ptr(gx), _ptr(gy), _ptr(gs), _stream_handle(self.device))
+        return gs
+
+    def kernel_tables(self):
+        """FP64 quarter tables (w^x, w^y at 0 <= m < nx, 0 <= n < ny) copied to the host."""
+        import numpy as np
+        wx = np.empty((self.nx, self.ny))
+        wy = np.empty((self.nx, self.ny))
+        native.call("tdg_copy_kernel_tables", self._h, wx.ctypes.data, wy.ctypes.data)
+        return wx, wy
+
+    def device_error(self) -> int:
+        return int(native.load().tdg_get_device_error(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            native.load().tdg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def forces_batched(plans: list[Plan], sigmas: list[torch.Tensor], outs: list[tuple] | None = None):
+    """Solve many independent grids in one library call."""
+    n = len(plans)
+    if outs is None:
+        outs = [(torch.empty_like(s), torch.empty_like(s)) for s in sigmas]
+    for p, s, (fx, fy) in zip(plans, sigmas, outs):
+        p._check(s, "sigma")
+        p._check(fx, "fx")
+        p._check(fy, "fy")
+    arr = ctypes.c_void_p * n
+    hs = arr(*[p.handle.value for p in plans])
+    ss = arr(*[_ptr(s) for s in sigmas])
+    xs = arr(*[_ptr(o[0]) for o in outs])
+    ys = arr(*[_ptr(o[1]) for o in outs])
+    dev = plans[0].device if plans else torch.device("cuda", 0)
+    native.call("tdg_solve_forces_batched", hs, n, ss, xs, ys, _stream_handle(dev))
+    return outs
+
+
+class ThinDiskForces(torch.autograd.Function):
+    """(F^x, F^y) = solve(sigma) with the backward given by the library's adjoint."""
+
+    @staticmethod
+    def forward(ctx, plan: Plan, sigma: torch.Tensor):
+        ctx.plan = plan
+        return plan.forces(sigma.contiguous())
+
+    @staticmethod
+    def backward(ctx, gx, gy):
+        plan = ctx.plan
+        gx = torch.zeros((plan.nx, plan.ny), dtype=plan.dtype, device=plan.device) if gx is None else gx.contiguous()
+        gy = torch.zeros((plan.nx, plan.ny), dtype=plan.dtype, device=plan.device) if gy is None else gy.contiguous()
+        return None, plan.adjoint(gx, gy)

@@ -1,0 +1,516 @@
+// The three passes of the force solve and of its adjoint (Sec. 4.1: one forward transform
+// of C, two inverse transforms), plus the forward transform of the kernel tables.
+//
+// Data flow of a forward solve (P_x, P_y the padded periods, M = P_y / 2, hy = M + 1):
+//   pass A (rows, y):    sigma row -> [order 3: tridiagonal solve along y] -> zero-pad to
+//                        P_y -> real transform (complex length-M FFT + unpacking) ->
+//                        hy frequencies written to the tiled buffer Z
+//   pass B (columns, x): Z column ky -> [order 3: tridiagonal solve along x on the complex
+//                        column, which commutes with the y transform] -> zero-pad to P_x
+//                        -> FFT -> times i s_x and i s_y -> two inverse FFTs -> first nx
+//                        rows written to the tiled buffers G_x, G_y
+//   pass C (rows, y):    G row -> Hermitian repacking -> inverse complex FFT of length M ->
+//                        first ny reals = F^x (resp. F^y)
+// The adjoint runs the transposed chain: A on g_x and g_y, B with the conjugate spectra
+// (correlation) summed into one column and the x solve after the crop, C with the y solve
+// after the crop.
+//
+// Tiled intermediates: element (row i, frequency ky) of an nx x hy complex array lives at
+// [ky / TW][i][ky % TW]; a pass-B column is a strided walk through one contiguous slab and
+// the row passes move whole TW-wide slices of TR rows.
+#include <cuda_runtime.h>
+
+#include "fft_block.cuh"
+#include "tdg_internal.cuh"
+
+namespace tdg {
+
+template <typename T> struct RowCfg;
+template <> struct RowCfg<float> { static constexpr int TR = 4; static constexpr int TW = 4; };
+template <> struct RowCfg<double> { static constexpr int TR = 2; static constexpr int TW = 2; };
+
+constexpr int kEPT = 16;  // elements per thread held in registers by one FFT stage
+
+struct Tiled {
+    int tw;           // tile width
+    size_t slab;      // elements per tile slab = rows * tw
+};
+
+__device__ __forceinline__ size_t tidx(const Tiled& t, int row, int ky) {
+    return (size_t)(ky / t.tw) * t.slab + (size_t)row * t.tw + (ky % t.tw);
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> r2c_unpack(cpx<T> za, cpx<T> zb, cpx<T> w) {
+    // X = (Za + conj Zb)/2 - i w (Za - conj Zb)/2
+    cpx<T> e = mk(T(0.5) * (za.x + zb.x), T(0.5) * (za.y - zb.y));
+    cpx<T> d = mk(T(0.5) * (za.x - zb.x), T(0.5) * (za.y + zb.y));
+    cpx<T> wd = cmul(w, d);
+    return mk(e.x + wd.y, e.y - wd.x);
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> c2r_pack(cpx<T> xa, cpx<T> xb, cpx<T> w) {
+    // Z = (Xa + conj Xb) + i conj(w) (Xa - conj Xb)
+    cpx<T> e = mk(xa.x + xb.x, xa.y - xb.y);
+    cpx<T> d = mk(xa.x - xb.x, xa.y + xb.y);
+    cpx<T> wd = cmulc(d, w);
+    return mk(e.x - wd.y, e.y + wd.x);
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass A: real rows -> hy complex frequencies (tiled output).
+// in: rows of `ld` reals, the first `ncols` valid (the rest of the period is zero).
+// ---------------------------------------------------------------------------------------
+template <typename T> struct Bounds;
+template <> struct Bounds<float> { static constexpr int ROWS = 1024; };
+template <> struct Bounds<double> { static constexpr int ROWS = 512; };
+constexpr int kColThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(Bounds<T>::ROWS) k_rows_r2c(const T* __restrict__ in, int nrows, int ld, int ncols,
+                                                   int solve, FftPlan fp, const cpx<T>* __restrict__ tw,
+                                                   cpx<T>* __restrict__ out, Tiled ot, int hy) {
+    constexpr int TR = RowCfg<T>::TR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = fp.L;
+    cpx<T>* cbuf = reinterpret_cast<cpx<T>*>(smem_raw);                 // (M + 1) * TR
+    T* rbuf = reinterpret_cast<T*>(cbuf + (size_t)(M + 1) * TR);        // ncols * TR
+    T* lam = rbuf + (size_t)ncols * TR;                                 // kLamTable
+    const int r0 = blockIdx.x * TR;
+    const int nr = min(TR, nrows - r0);
+
+    if (solve) {
+        for (int idx = threadIdx.x; idx < TR * ncols; idx += blockDim.x) {
+            int c = idx / ncols, j = idx % ncols;
+            rbuf[j * TR + c] = (c < nr) ? in[(size_t)(r0 + c) * ld + j] : T(0);
+        }
+        init_lambda(lam);
+        __syncthreads();
+        tridiag_solve_lines<T, T>(rbuf, reinterpret_cast<T*>(cbuf), rbuf, ncols, TR, lam);
+        // pack z[n] = x[2n] + i x[2n+1], x zero beyond ncols
+        for (int idx = threadIdx.x; idx < TR * M; idx += blockDim.x) {
+            int c = idx % TR, n = idx / TR;
+            int j0 = 2 * n, j1 = 2 * n + 1;
+            T a = (j0 < ncols) ? rbuf[j0 * TR + c] : T(0);
+            T b = (j1 < ncols) ? rbuf[j1 * TR + c] : T(0);
+            cbuf[n * TR + c] = mk(a, b);
+        }
+    } else {
+        // pack straight from the rows
+        for (int idx = threadIdx.x; idx < TR * M; idx += blockDim.x) {
+            int c = idx / M, n = idx % M;
+            int j0 = 2 * n, j1 = 2 * n + 1;
+            const T* row = in + (size_t)(r0 + c) * ld;
+            T a = (c < nr && j0 < ncols) ? row[j0] : T(0);
+            T b = (c < nr && j1 < ncols) ? row[j1] : T(0);
+            cbuf[n * TR + c] = mk(a, b);
+        }
+    }
+    __syncthreads();
+    fft_lines<T, kEPT>(cbuf, fp, TR, tw, 2, false);
+
+    // unpack to X[k], k = 0..M; thread owns the pair (k, M - k)
+    const int half = M / 2;
+    for (int idx = threadIdx.x; idx < TR * (half + 1); idx += blockDim.x) {
+        int c = idx % TR, k = idx / TR;
+        if (k == 0) {
+            cpx<T> z0 = cbuf[c];
+            cbuf[c] = mk(z0.x + z0.y, T(0));
+            cbuf[M * TR + c] = mk(z0.x - z0.y, T(0));
+        } else if (2 * k == M) {
+            cpx<T> z = cbuf[k * TR + c];
+            cbuf[k * TR + c] = r2c_unpack(z, z, ldg_c(tw + k));
+        } else {
+            cpx<T> za = cbuf[k * TR + c], zb = cbuf[(M - k) * TR + c];
+            cbuf[k * TR + c] = r2c_unpack(za, zb, ldg_c(tw + k));
+            cbuf[(M - k) * TR + c] = r2c_unpack(zb, za, ldg_c(tw + (M - k)));
+        }
+    }
+    __syncthreads();
+
+    // tiled write: for each slab, TR rows x TW frequencies are contiguous
+    const int TW = ot.tw;
+    const int ntile = (hy + TW - 1) / TW;
+    for (int idx = threadIdx.x; idx < ntile * TR * TW; idx += blockDim.x) {
+        int w = idx % TW, c = (idx / TW) % TR, t = idx / (TW * TR);
+        int ky = t * TW + w;
+        if (c < nr && ky < hy) out[tidx(ot, r0 + c, ky)] = cbuf[ky * TR + c];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass C: hy complex frequencies -> real rows (first ncols of the period), optional
+// tridiagonal solve along the row after the crop (adjoint).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(Bounds<T>::ROWS) k_rows_c2r(const cpx<T>* __restrict__ in0, const cpx<T>* __restrict__ in1,
+                                                   Tiled it, int nrows, int hy, int solve, FftPlan fp,
+                                                   const cpx<T>* __restrict__ tw, T* __restrict__ out0,
+                                                   T* __restrict__ out1, int ncols) {
+    constexpr int TR = RowCfg<T>::TR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = fp.L;
+    cpx<T>* cbuf = reinterpret_cast<cpx<T>*>(smem_raw);
+    T* rbuf = reinterpret_cast<T*>(cbuf + (size_t)(M + 1) * TR);
+    T* lam = rbuf + (size_t)ncols * TR;
+    const cpx<T>* in = blockIdx.y ? in1 : in0;
+    T* out = blockIdx.y ? out1 : out0;
+    const int r0 = blockIdx.x * TR;
+    const int nr = min(TR, nrows - r0);
+    const int TW = it.tw;
+    const int ntile = (hy + TW - 1) / TW;
+
+    for (int idx = threadIdx.x; idx < ntile * TR * TW; idx += blockDim.x) {
+        int w = idx % TW, c = (idx / TW) % TR, t = idx / (TW * TR);
+        int ky = t * TW + w;
+        if (ky < hy) cbuf[ky * TR + c] = (c < nr) ? in[tidx(it, r0 + c, ky)] : mk(T(0), T(0));
+    }
+    if (solve) init_lambda(lam);
+    __syncthreads();
+
+    // Hermitian repack into Z[k], k < M; thread owns the pair (k, M - k)
+    const int half = M / 2;
+    for (int idx = threadIdx.x; idx < TR * (half + 1); idx += blockDim.x) {
+        int c = idx % TR, k = idx / TR;
+        if (k == 0) {
+            cpx<T> x0 = cbuf[c], xm = cbuf[M * TR + c];
+            cbuf[c] = c2r_pack(x0, xm, mk(T(1), T(0)));
+        } else if (2 * k == M) {
+            cpx<T> x = cbuf[k * TR + c];
+            cbuf[k * TR + c] = c2r_pack(x, x, ldg_c(tw + k));
+        } else {
+            cpx<T> xa = cbuf[k * TR + c], xb = cbuf[(M - k) * TR + c];
+            cbuf[k * TR + c] = c2r_pack(xa, xb, ldg_c(tw + k));
+            cbuf[(M - k) * TR + c] = c2r_pack(xb, xa, ldg_c(tw + (M - k)));
+        }
+    }
+    __syncthreads();
+    fft_lines<T, kEPT>(cbuf, fp, TR, tw, 2, true);
+
+    if (!solve) {
+        for (int idx = threadIdx.x; idx < TR * ncols; idx += blockDim.x) {
+            int c = idx / ncols, j = idx % ncols;
+            if (c < nr) {
+                cpx<T> z = cbuf[(j >> 1) * TR + c];
+                out[(size_t)(r0 + c) * ncols + j] = (j & 1) ? z.y : z.x;
+            }
+        }
+        return;
+    }
+    for (int idx = threadIdx.x; idx < TR * ncols; idx += blockDim.x) {
+        int c = idx % TR, j = idx / TR;
+        cpx<T> z = cbuf[(j >> 1) * TR + c];
+        rbuf[j * TR + c] = (j & 1) ? z.y : z.x;
+    }
+    __syncthreads();
+    tridiag_solve_lines<T, T>(rbuf, reinterpret_cast<T*>(cbuf), rbuf, ncols, TR, lam);
+    for (int idx = threadIdx.x; idx < TR * ncols; idx += blockDim.x) {
+        int c = idx / ncols, j = idx % ncols;
+        if (c < nr) out[(size_t)(r0 + c) * ncols + j] = rbuf[j * TR + c];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass B (forward): one column ky per block.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void load_column(cpx<T>* s, const cpx<T>* __restrict__ z, const Tiled& t, int ky,
+                                            int nx, int P) {
+    for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = (i < nx) ? z[tidx(t, i, ky)] : mk(T(0), T(0));
+}
+
+// s holds the column in [0, nx) and zeros beyond; solves along x in place, restores zeros
+template <typename T>
+__device__ __forceinline__ void column_solve(cpx<T>* s, int nx, int P, const T* lam) {
+    tridiag_solve_lines<T, cpx<T>>(s, s + nx, s, nx, 1, lam);
+    for (int i = nx + threadIdx.x; i < P; i += blockDim.x) s[i] = mk(T(0), T(0));
+    __syncthreads();
+}
+
+template <typename T, bool KEEP>
+__global__ void __launch_bounds__(kColThreads) k_cols_conv(const cpx<T>* __restrict__ z, Tiled t, int nx, int hy,
+                                                    int solve, FftPlan fp, const cpx<T>* __restrict__ tw,
+                                                    const T* __restrict__ spec, cpx<T>* __restrict__ gx,
+                                                    cpx<T>* __restrict__ gy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = fp.L;
+    cpx<T>* s = reinterpret_cast<cpx<T>*>(smem_raw);
+    T* lam = reinterpret_cast<T*>(s + P);
+    const int ky = blockIdx.x;
+    const size_t sstride = (size_t)hy * P;
+    cpx<T> keep[KEEP ? kEPT : 1];
+
+    for (int comp = 0; comp < 2; ++comp) {
+        if (comp == 0 || !KEEP) {
+            load_column(s, z, t, ky, nx, P);
+            if (solve) init_lambda(lam);
+            __syncthreads();
+            if (solve) column_solve(s, nx, P, lam);
+            fft_lines<T, kEPT>(s, fp, 1, tw, 1, false);
+            if (KEEP) {
+#pragma unroll
+                for (int q = 0; q < kEPT; ++q) {
+                    int e = threadIdx.x + q * blockDim.x;
+                    if (e < P) keep[q] = s[e];
+                }
+                __syncthreads();
+            }
+        }
+        const T* sc = spec + comp * sstride + (size_t)ky * P;
+        cpx<T>* g = comp ? gy : gx;
+        // times i s_c
+        if (KEEP) {
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) {
+                int e = threadIdx.x + q * blockDim.x;
+                if (e < P) {
+                    T sv = __ldg(sc + e);
+                    s[e] = mk(-sv * keep[q].y, sv * keep[q].x);
+                }
+            }
+        } else {
+            for (int e = threadIdx.x; e < P; e += blockDim.x) {
+                T sv = __ldg(sc + e);
+                cpx<T> v = s[e];
+                s[e] = mk(-sv * v.y, sv * v.x);
+            }
+        }
+        __syncthreads();
+        fft_lines<T, kEPT>(s, fp, 1, tw, 1, true);
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) g[tidx(t, i, ky)] = s[i];
+        __syncthreads();
+    }
+}
+
+// Pass B (adjoint): dL/dC-hat = -i (s_x Gx-hat + s_y Gy-hat), one inverse FFT, crop,
+// x solve after the crop.
+template <typename T>
+__global__ void __launch_bounds__(kColThreads) k_cols_adj(const cpx<T>* __restrict__ zx, const cpx<T>* __restrict__ zy,
+                                                   Tiled t, int nx, int hy, int solve, FftPlan fp,
+                                                   const cpx<T>* __restrict__ tw, const T* __restrict__ spec,
+                                                   cpx<T>* __restrict__ gout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = fp.L;
+    cpx<T>* s = reinterpret_cast<cpx<T>*>(smem_raw);
+    T* lam = reinterpret_cast<T*>(s + P);
+    const int ky = blockIdx.x;
+    const size_t sstride = (size_t)hy * P;
+    cpx<T> acc[kEPT];
+
+    for (int comp = 0; comp < 2; ++comp) {
+        load_column(s, comp ? zy : zx, t, ky, nx, P);
+        __syncthreads();
+        fft_lines<T, kEPT>(s, fp, 1, tw, 1, false);
+        const T* sc = spec + comp * sstride + (size_t)ky * P;
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) {
+            int e = threadIdx.x + q * blockDim.x;
+            if (e < P) {
+                T sv = __ldg(sc + e);
+                cpx<T> v = s[e];
+                // -i s v
+                cpx<T> r = mk(sv * v.y, -sv * v.x);
+                acc[q] = comp ? acc[q] + r : r;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < kEPT; ++q) {
+        int e = threadIdx.x + q * blockDim.x;
+        if (e < P) s[e] = acc[q];
+    }
+    if (solve) init_lambda(lam);
+    __syncthreads();
+    fft_lines<T, kEPT>(s, fp, 1, tw, 1, true);
+    if (solve) column_solve(s, nx, P, lam);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) gout[tidx(t, i, ky)] = s[i];
+}
+
+// Spectrum of the placed tables: column FFT of the row-transformed tables, keep the
+// imaginary part (the tables are odd along the force axis) scaled by G / (P_x P_y).
+template <typename T>
+__global__ void __launch_bounds__(kColThreads) k_cols_spectrum(const cpx<double>* __restrict__ z, Tiled t, int hy,
+                                                        FftPlan fp, const cpx<double>* __restrict__ tw,
+                                                        double scale, T* __restrict__ spec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = fp.L;
+    cpx<double>* s = reinterpret_cast<cpx<double>*>(smem_raw);
+    const int ky = blockIdx.x;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = z[tidx(t, i, ky)];
+    __syncthreads();
+    fft_lines<double, kEPT>(s, fp, 1, tw, 1, false);
+    for (int e = threadIdx.x; e < P; e += blockDim.x) spec[(size_t)ky * P + e] = T(scale * s[e].y);
+}
+
+template <typename T>
+__global__ void k_twiddles(cpx<T>* tw, int P) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) {
+        double sn, cs;
+        sincospi(2.0 * (double)k / (double)P, &sn, &cs);
+        tw[k] = mk(T(cs), T(-sn));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------
+
+static int round_threads(long work, int cap) {
+    long nt = (work + kEPT - 1) / kEPT;
+    nt = ((nt + 31) / 32) * 32;
+    if (nt < 64) nt = 64;
+    if (nt > cap) nt = cap;
+    return (int)nt;
+}
+
+template <typename T>
+static size_t row_smem(int M, int ncols, int solve) {
+    if (!solve) ncols = 0;
+    constexpr int TR = RowCfg<T>::TR;
+    return (size_t)(M + 1) * TR * sizeof(cpx<T>) + (size_t)ncols * TR * sizeof(T) + kLamTable * sizeof(T);
+}
+
+template <typename T>
+static size_t col_smem(int P) {
+    return (size_t)P * sizeof(cpx<T>) + kLamTable * sizeof(T);
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T>
+static cudaError_t rows_r2c(const T* in, int nrows, int ld, int ncols, int solve, const FftPlan& fp,
+                            const cpx<T>* tw, cpx<T>* out, Tiled ot, int hy, cudaStream_t s) {
+    constexpr int TR = RowCfg<T>::TR;
+    size_t sm = row_smem<T>(fp.L, ncols, solve);
+    cudaError_t e = set_smem(k_rows_r2c<T>, sm);
+    if (e != cudaSuccess) return e;
+    int nt = round_threads((long)TR * fp.L, Bounds<T>::ROWS);
+    k_rows_r2c<T><<<(nrows + TR - 1) / TR, nt, sm, s>>>(in, nrows, ld, ncols, solve, fp, tw, out, ot, hy);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t rows_c2r(const cpx<T>* in0, const cpx<T>* in1, Tiled it, int nrows, int hy, int solve,
+                            const FftPlan& fp, const cpx<T>* tw, T* out0, T* out1, int ncols, cudaStream_t s) {
+    constexpr int TR = RowCfg<T>::TR;
+    size_t sm = row_smem<T>(fp.L, ncols, solve);
+    cudaError_t e = set_smem(k_rows_c2r<T>, sm);
+    if (e != cudaSuccess) return e;
+    int nt = round_threads((long)TR * fp.L, Bounds<T>::ROWS);
+    dim3 grid((nrows + TR - 1) / TR, in1 ? 2 : 1);
+    k_rows_c2r<T><<<grid, nt, sm, s>>>(in0, in1, it, nrows, hy, solve, fp, tw, out0, out1, ncols);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static Tiled tiled_of(const Plan& p, int rows) {
+    Tiled t;
+    t.tw = RowCfg<T>::TW;
+    t.slab = (size_t)rows * t.tw;
+    return t;
+}
+
+template <typename T>
+cudaError_t launch_twiddles(cpx<T>* tw, int P, cudaStream_t s) {
+    k_twiddles<T><<<(P + 255) / 256, 256, 0, s>>>(tw, P);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* work, cudaStream_t s) {
+    const Tiled t = tiled_of<T>(p, p.nx);
+    const size_t n_el = (size_t)p.ntile * t.slab;
+    cpx<T>* z = reinterpret_cast<cpx<T>*>(work);
+    cpx<T>* gx = z + n_el;
+    cpx<T>* gy = gx + n_el;
+    const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
+    const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
+    const int solve = p.order == 3;
+    cudaError_t e = rows_r2c<T>(sigma, p.nx, p.ny, p.ny, solve, p.ay.half, twy, z, t, p.hy, s);
+    if (e != cudaSuccess) return e;
+    // one column per block; FP32 keeps the transformed column in registers, FP64 redoes
+    // the forward transform for the second component (register budget)
+    constexpr bool KEEP = sizeof(T) == 4;
+    size_t sm = col_smem<T>(p.ax.full.L);
+    e = set_smem(k_cols_conv<T, KEEP>, sm);
+    if (e != cudaSuccess) return e;
+    int nt = round_threads(p.ax.full.L, kColThreads);
+    k_cols_conv<T, KEEP><<<p.hy, nt, sm, s>>>(z, t, p.nx, p.hy, solve, p.ax.full, twx,
+                                              reinterpret_cast<const T*>(p.spec), gx, gy);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return rows_c2r<T>(gx, gy, t, p.nx, p.hy, 0, p.ay.half, twy, fx, fy, p.ny, s);
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const Plan& p, const T* gxin, const T* gyin, T* gsig, void* work, cudaStream_t s) {
+    const Tiled t = tiled_of<T>(p, p.nx);
+    const size_t n_el = (size_t)p.ntile * t.slab;
+    cpx<T>* zx = reinterpret_cast<cpx<T>*>(work);
+    cpx<T>* zy = zx + n_el;
+    cpx<T>* gc = zy + n_el;
+    const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
+    const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
+    const int solve = p.order == 3;
+    cudaError_t e = rows_r2c<T>(gxin, p.nx, p.ny, p.ny, 0, p.ay.half, twy, zx, t, p.hy, s);
+    if (e != cudaSuccess) return e;
+    e = rows_r2c<T>(gyin, p.nx, p.ny, p.ny, 0, p.ay.half, twy, zy, t, p.hy, s);
+    if (e != cudaSuccess) return e;
+    size_t sm = col_smem<T>(p.ax.full.L);
+    e = set_smem(k_cols_adj<T>, sm);
+    if (e != cudaSuccess) return e;
+    int nt = round_threads(p.ax.full.L, kColThreads);
+    k_cols_adj<T><<<p.hy, nt, sm, s>>>(zx, zy, t, p.nx, p.hy, solve, p.ax.full, twx,
+                                       reinterpret_cast<const T*>(p.spec), gc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return rows_c2r<T>(gc, nullptr, t, p.nx, p.hy, solve, p.ay.half, twy, gsig, nullptr, p.ny, s);
+}
+
+template <typename T>
+cudaError_t launch_spectra(const Plan& p, const double* placed_x, const double* placed_y, void* scratch,
+                           T* spec, cudaStream_t s) {
+    // FP64 transforms of the two placed P_x x P_y tables (twiddles in FP64)
+    const int Px = p.ax.P, Py = p.ay.P;
+    Tiled t;
+    t.tw = RowCfg<double>::TW;
+    t.slab = (size_t)Px * t.tw;
+    cpx<double>* z = reinterpret_cast<cpx<double>*>(scratch);
+    cudaError_t e;
+    // twiddle tables in FP64 for this build (the plan's own may be FP32)
+    cpx<double>* tw64x = z + (size_t)((p.hy + t.tw - 1) / t.tw) * t.slab;
+    cpx<double>* tw64y = tw64x + Px;
+    if ((e = launch_twiddles<double>(tw64x, Px, s)) != cudaSuccess) return e;
+    if ((e = launch_twiddles<double>(tw64y, Py, s)) != cudaSuccess) return e;
+    const double scale = p.G / ((double)Px * (double)Py);
+    size_t sm = col_smem<double>(Px);
+    if ((e = set_smem(k_cols_spectrum<T>, sm)) != cudaSuccess) return e;
+    int nt = round_threads(Px, kColThreads);
+    for (int comp = 0; comp < 2; ++comp) {
+        const double* placed = comp ? placed_y : placed_x;
+        e = rows_r2c<double>(placed, Px, Py, Py, 0, p.ay.half, tw64y, z, t, p.hy, s);
+        if (e != cudaSuccess) return e;
+        k_cols_spectrum<T><<<p.hy, nt, sm, s>>>(z, t, p.hy, p.ax.full, tw64x, scale,
+                                                spec + (size_t)comp * p.hy * Px);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template cudaError_t launch_twiddles<float>(cpx<float>*, int, cudaStream_t);
+template cudaError_t launch_twiddles<double>(cpx<double>*, int, cudaStream_t);
+template cudaError_t launch_forward<float>(const Plan&, const float*, float*, float*, void*, cudaStream_t);
+template cudaError_t launch_forward<double>(const Plan&, const double*, double*, double*, void*, cudaStream_t);
+template cudaError_t launch_adjoint<float>(const Plan&, const float*, const float*, float*, void*, cudaStream_t);
+template cudaError_t launch_adjoint<double>(const Plan&, const double*, const double*, double*, void*,
+                                            cudaStream_t);
+template cudaError_t launch_spectra<float>(const Plan&, const double*, const double*, void*, float*,
+                                           cudaStream_t);
+template cudaError_t launch_spectra<double>(const Plan&, const double*, const double*, void*, double*,
+                                            cudaStream_t);
+
+}  // namespace tdg

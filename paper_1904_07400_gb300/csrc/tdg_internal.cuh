@@ -1,0 +1,98 @@
+// Internal declarations shared by the tdgrav translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tdgrav.h"
+
+namespace tdg {
+
+template <typename T>
+struct cpx {
+    T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> mk(T a, T b) {
+    cpx<T> r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> conjg(cpx<T> a) { return mk(a.x, -a.y); }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> scl(cpx<T> a, T s) { return mk(a.x * s, a.y * s); }
+
+// Maximum number of radix stages of one transform.
+constexpr int kMaxStages = 16;
+
+// Radix schedule of one transform length L = prod radix[s] (radices 2, 3, 4, 8).
+struct FftPlan {
+    int L;
+    int nst;
+    int radix[kMaxStages];
+};
+
+// Per-axis description used by the kernels.
+struct AxisInfo {
+    int n;        // cells along the axis
+    int P;        // padded period (even, 2^a 3^b, >= 2n - 1)
+    FftPlan half; // complex transform of length P/2 (rows: real transform of length P)
+    FftPlan full; // complex transform of length P (columns)
+};
+
+struct Plan {
+    int nx, ny, order, device;
+    double dx, dy, G;
+    tdg_precision prec;
+    AxisInfo ax, ay;       // x: columns (axis 0), y: rows (axis 1, contiguous)
+    int hy;                // number of y frequencies kept: P_y/2 + 1
+    int tw;                // tile width (complex elements) of the tiled intermediates
+    int ntile;             // ceil(hy / tw)
+    size_t ld_tile;        // elements per tile slab: nx * tw
+    size_t elem;           // sizeof(real)
+    bool built;
+    // device allocations
+    void* tw_x;            // twiddles exp(-2 pi i k / P_x), k < P_x, complex<real>
+    void* tw_y;            // twiddles exp(-2 pi i k / P_y), k < P_y
+    void* spec;            // spectra s_x, s_y: 2 x hy x P_x reals, layout [c][ky][kx]
+    double* wq;            // FP64 quarter tables w^x, w^y: 2 x nx x ny (kept for tests)
+    void* work;            // workspace (plan-owned or caller-owned)
+    size_t work_bytes;
+    bool work_owned;
+    int* err;              // device error word
+};
+
+size_t workspace_bytes(const Plan& p);
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_build_tables(const Plan& p, double* wq, double* placed_x, double* placed_y,
+                                const double* glx, const double* glw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_twiddles(cpx<T>* tw, int P, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spectra(const Plan& p, const double* placed_x, const double* placed_y,
+                           void* scratch, T* spec, cudaStream_t s);
+template <typename T>
+cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* work,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint(const Plan& p, const T* gx, const T* gy, T* gsig, void* work,
+                           cudaStream_t s);
+
+}  // namespace tdg

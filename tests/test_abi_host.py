@@ -1,0 +1,151 @@
+"""The C-ABI library without a GPU: it loads, exports every declared symbol, validates
+arguments on the host, and its host-callable table-entry code matches the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1904_07400_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tdgrav.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_07400_gb300 import build
+    build.build()
+    return native.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tdg_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(n for n, _, _ in native.SIGNATURES) == names
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        s = lib.tdg_status_string(code)
+        assert isinstance(s, bytes) and len(s) > 0
+    assert lib.tdg_status_string(0) == b"ok"
+
+
+def _init(lib, *args):
+    h = ctypes.c_void_p()
+    st = lib.tdg_init(ctypes.byref(h), *args)
+    return st, h
+
+
+def test_init_validates_arguments(lib):
+    ok = (64, 64, 3, 0.1, 0.1, 1.0, 1, 0)
+    st, h = _init(lib, *ok)
+    assert st == 0 and h.value
+    px, py = ctypes.c_int(), ctypes.c_int()
+    assert lib.tdg_plan_info(h, ctypes.byref(px), ctypes.byref(py), None, None) == 0
+    assert (px.value, py.value) == (128, 128)
+    assert lib.tdg_destroy(h) == 0
+    bad = [
+        (64, 64, 0, 0.1, 0.1, 1.0, 1, 0),      # order
+        (64, 64, 4, 0.1, 0.1, 1.0, 1, 0),
+        (0, 64, 3, 0.1, 0.1, 1.0, 1, 0),       # size
+        (64, 64, 3, 0.0, 0.1, 1.0, 1, 0),      # spacing
+        (64, 64, 3, 0.1, -1.0, 1.0, 1, 0),
+        (64, 64, 3, float("nan"), 0.1, 1.0, 1, 0),
+        (64, 64, 3, 0.1, 0.1, float("inf"), 1, 0),
+        (64, 64, 3, 0.1, 0.1, 1.0, 7, 0),      # precision
+        (64, 64, 3, 0.1, 0.1, 1.0, 1, -1),     # device
+    ]
+    for args in bad:
+        st, h = _init(lib, *args)
+        assert st == 1 and not h.value, args
+    st, _ = _init(lib, 4097, 64, 3, 0.1, 0.1, 1.0, 1, 0)
+    assert st == 2
+    assert lib.tdg_init(None, 64, 64, 3, 0.1, 0.1, 1.0, 1, 0) == 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 17, 33, 64, 100, 192, 4096])
+def test_padded_period_choice(lib, n):
+    st, h = _init(lib, n, 2, 1, 1.0, 1.0, 1.0, 0, 0)
+    assert st == 0
+    px = ctypes.c_int()
+    lib.tdg_plan_info(h, ctypes.byref(px), None, None, None)
+    p = px.value
+    q = p // 2
+    while q % 2 == 0:
+        q //= 2
+    while q % 3 == 0:
+        q //= 3
+    assert p % 2 == 0 and q == 1 and p >= 2 * n - 1 and p >= 2
+    lib.tdg_destroy(h)
+
+
+def test_solve_before_build_and_null_pointers(lib):
+    st, h = _init(lib, 16, 16, 2, 0.1, 0.1, 1.0, 1, 0)
+    assert lib.tdg_solve_forces(h, 256, 512, 768, None) == 3          # NOT_BUILT
+    assert lib.tdg_solve_forces(h, None, 512, 768, None) == 1         # null
+    assert lib.tdg_solve_forces(h, 257, 512, 768, None) == 1          # misaligned
+    assert lib.tdg_solve_adjoint(h, 256, 512, 768, None) == 3
+    wx = np.zeros(256)
+    assert lib.tdg_copy_kernel_tables(h, wx.ctypes.data, wx.ctypes.data) == 3
+    assert lib.tdg_workspace_bytes(h) > 0
+    assert lib.tdg_set_workspace(h, 1024 + 8, 1 << 30) == 1           # not 256-aligned
+    assert lib.tdg_set_workspace(h, 4096, 16) == 1                    # too small
+    lib.tdg_destroy(h)
+
+
+def test_kernel_entry_host_matches_oracle_near_field(lib):
+    from oracle import kernel_tables as kt
+    worst = 0.0
+    for k in (1, 2, 3):
+        for ratio in (1.0, 0.5, 8.0):
+            for m in range(4):
+                for n in range(4):
+                    for comp in (0, 1):
+                        got = native.kernel_entry_host(k, m, n, 1.0, ratio, comp)
+                        ref = kt._near_entry(k, m, n, ratio, "xy"[comp])
+                        if ref == 0.0:
+                            assert got == 0.0
+                            continue
+                        worst = max(worst, abs(got - ref) / abs(ref))
+    assert worst < 5e-15
+
+
+def test_kernel_entry_host_matches_oracle_far_field(lib):
+    from oracle import kernel_tables as kt
+    rng = np.random.default_rng(0)
+    for k in (1, 2, 3):
+        for ratio in (1.0, 0.25, 3.0):
+            ms = rng.integers(-300, 300, 30)
+            ns = rng.integers(-300, 300, 30)
+            for comp in ("x", "y"):
+                d = kt.effective_distance(ms, ns, 1.0, ratio)
+                for m, n, dd in zip(ms, ns, d):
+                    if max(abs(m), abs(n)) < kt.NEAR_FIELD:
+                        continue
+                    q = [q for lim, q in kt.FAR_BANDS if lim is None or dd < lim][0]
+                    ref = kt.w_far_gl(k, np.array([m]), np.array([n]), 1.0, ratio, q, comp)[0]
+                    got = native.kernel_entry_host(k, int(m), int(n), 1.0, ratio, "xy".index(comp))
+                    if ref == 0.0:
+                        assert got == 0.0
+                    else:
+                        assert abs(got - ref) < 1e-14 * abs(ref), (k, ratio, m, n, comp)
+
+
+def test_kernel_entry_host_symmetries(lib):
+    e = native.kernel_entry_host
+    for k in (1, 2, 3):
+        assert e(k, 3, 5, 1.0, 1.0, 0) == -e(k, -3, 5, 1.0, 1.0, 0)
+        assert e(k, 3, 5, 1.0, 1.0, 0) == e(k, 3, -5, 1.0, 1.0, 0)
+        assert e(k, 3, 5, 1.0, 1.0, 1) == e(k, 5, 3, 1.0, 1.0, 0)
+        assert e(k, 0, 7, 1.0, 1.0, 0) == 0.0
