@@ -117,6 +117,14 @@ tdg_status tdg_copy_kernel_tables(const tdg_plan p, double* wx, double* wy);
 tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy,
                                  int component, double* out);
 
+/* Instrumentation: ask every later forward solve or adjoint of this plan to record the
+ * caller-owned CUDA events events[0..count-1] (cudaEvent_t handles) on its stream:
+ * events[0] before the first pass and events[i] after pass i (1: row transform, 2: column
+ * convolution, 3: row inverse transform), so that the caller can time each kernel on the
+ * stream it runs on.  count must be 0 (stop recording; events may be NULL) or 4.  The
+ * library never creates, destroys or synchronises these events.  Errors: INVALID_ARG. */
+tdg_status tdg_set_pass_events(tdg_plan p, void* const* events, int count);
+
 /* Transform lengths chosen for the plan: the padded periods px, py (even, 2^a 3^b,
  * >= 2n - 1) along x and y.  Any out pointer may be NULL. */
 tdg_status tdg_plan_info(const tdg_plan p, int* px, int* py, int* order, int* precision);

@@ -421,6 +421,16 @@ tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy, 
     return TDG_OK;
 }
 
+tdg_status tdg_set_pass_events(tdg_plan h, void* const* events, int count) {
+    if (!h || (count != 0 && count != 4) || (count == 4 && !events)) return TDG_ERR_INVALID_ARG;
+    Plan& p = h->p;
+    for (int i = 0; i < count; ++i)
+        if (!events[i]) return TDG_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) p.ev[i] = reinterpret_cast<cudaEvent_t>(events[i]);
+    p.n_ev = count;
+    return TDG_OK;
+}
+
 tdg_status tdg_plan_info(const tdg_plan h, int* px, int* py, int* order, int* precision) {
     if (!h) return TDG_ERR_INVALID_ARG;
     if (px) *px = h->p.ax.P;

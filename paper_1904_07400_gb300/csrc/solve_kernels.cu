@@ -432,8 +432,10 @@ cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* wo
     const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
     const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
     const int solve = p.order == 3;
+    mark(p, 0, s);
     cudaError_t e = rows_r2c<T>(sigma, p.nx, p.ny, p.ny, solve, p.ay.half, twy, z, t, p.hy, s);
     if (e != cudaSuccess) return e;
+    mark(p, 1, s);
     // one column per block; FP32 keeps the transformed column in registers, FP64 redoes
     // the forward transform for the second component (register budget)
     constexpr bool KEEP = sizeof(T) == 4;
@@ -444,7 +446,10 @@ cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* wo
     k_cols_conv<T, KEEP><<<p.hy, nt, sm, s>>>(z, t, p.nx, p.hy, solve, p.ax.full, twx,
                                               reinterpret_cast<const T*>(p.spec), gx, gy);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return rows_c2r<T>(gx, gy, t, p.nx, p.hy, 0, p.ay.half, twy, fx, fy, p.ny, s);
+    mark(p, 2, s);
+    e = rows_c2r<T>(gx, gy, t, p.nx, p.hy, 0, p.ay.half, twy, fx, fy, p.ny, s);
+    mark(p, 3, s);
+    return e;
 }
 
 template <typename T>
@@ -457,10 +462,12 @@ cudaError_t launch_adjoint(const Plan& p, const T* gxin, const T* gyin, T* gsig,
     const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
     const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
     const int solve = p.order == 3;
+    mark(p, 0, s);
     cudaError_t e = rows_r2c<T>(gxin, p.nx, p.ny, p.ny, 0, p.ay.half, twy, zx, t, p.hy, s);
     if (e != cudaSuccess) return e;
     e = rows_r2c<T>(gyin, p.nx, p.ny, p.ny, 0, p.ay.half, twy, zy, t, p.hy, s);
     if (e != cudaSuccess) return e;
+    mark(p, 1, s);
     size_t sm = col_smem<T>(p.ax.full.L);
     e = set_smem(k_cols_adj<T>, sm);
     if (e != cudaSuccess) return e;
@@ -468,7 +475,10 @@ cudaError_t launch_adjoint(const Plan& p, const T* gxin, const T* gyin, T* gsig,
     k_cols_adj<T><<<p.hy, nt, sm, s>>>(zx, zy, t, p.nx, p.hy, solve, p.ax.full, twx,
                                        reinterpret_cast<const T*>(p.spec), gc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return rows_c2r<T>(gc, nullptr, t, p.nx, p.hy, solve, p.ay.half, twy, gsig, nullptr, p.ny, s);
+    mark(p, 2, s);
+    e = rows_c2r<T>(gc, nullptr, t, p.nx, p.hy, solve, p.ay.half, twy, gsig, nullptr, p.ny, s);
+    mark(p, 3, s);
+    return e;
 }
 
 template <typename T>

@@ -76,7 +76,14 @@ struct Plan {
     size_t work_bytes;
     bool work_owned;
     int* err;              // device error word
+    int n_ev;              // 0 or 4: events recorded around the passes (instrumentation)
+    cudaEvent_t ev[4];
 };
+
+// record the plan's instrumentation event i on stream s (no-op when none are set)
+inline void mark(const Plan& p, int i, cudaStream_t s) {
+    if (p.n_ev > i) cudaEventRecord(p.ev[i], s);
+}
 
 size_t workspace_bytes(const Plan& p);
 
