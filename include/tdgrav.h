@@ -125,6 +125,27 @@ tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy,
  * library never creates, destroys or synchronises these events.  Errors: INVALID_ARG. */
 tdg_status tdg_set_pass_events(tdg_plan p, void* const* events, int count);
 
+/* Size of the device array behind tdg_solve_forces_noalloc: 32 MiB. */
+#define TDG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* tdg_solve_forces without any allocation (the paper has no counterpart; this serves
+ * callers of the library).  Some callers cannot allocate device memory where they solve:
+ * code that runs while another allocator owns the device's free memory, real-time loops
+ * that must not hit cudaMalloc's implicit synchronisation, or hosts that forbid device
+ * allocations after start-up.  They build plans up front (tdg_init and
+ * tdg_build_kernel_tables allocate) and solve here: same inputs, outputs and results as
+ * tdg_solve_forces, but the scratch is a fixed device array of TDG_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits, and the call makes
+ * no cudaMalloc, cudaFree or other allocating call.
+ *   - The first call on a device looks up that array's device address (once per device,
+ *     with the device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents.  Calls that
+ *     overlap on the GPU (several streams or host threads) race on it: serialise them.
+ * Errors: UNSUPPORTED when tdg_workspace_bytes(p) > TDG_NOALLOC_SCRATCH_BYTES (about
+ * 1024 x 1024 in FP32, 724 x 724 in FP64); otherwise as tdg_solve_forces. */
+tdg_status tdg_solve_forces_noalloc(tdg_plan p, const void* sigma, void* fx, void* fy,
+                                    tdg_stream stream);
+
 /* Transform lengths chosen for the plan: the padded periods px, py (even, 2^a 3^b,
  * >= 2n - 1) along x and y.  Any out pointer may be NULL. */
 tdg_status tdg_plan_info(const tdg_plan p, int* px, int* py, int* order, int* precision);

@@ -16,6 +16,8 @@ struct tdg_plan_s {
     Plan p;
 };
 
+const Plan& tdg_plan_internal(const tdg_plan_s* h) { return h->p; }
+
 namespace {
 
 constexpr int kMaxN = 4096;            // longest grid side: P = 2M <= 8192 fits one block

@@ -87,6 +87,13 @@ inline void mark(const Plan& p, int i, cudaStream_t s) {
 
 size_t workspace_bytes(const Plan& p);
 
+}  // namespace tdg
+
+// the plan behind a C handle
+const tdg::Plan& tdg_plan_internal(const tdg_plan_s* h);
+
+namespace tdg {
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_build_tables(const Plan& p, double* wq, double* placed_x, double* placed_y,
                                 const double* glx, const double* glw, cudaStream_t s);

@@ -35,6 +35,7 @@ SIGNATURES = [
     ("tdg_copy_kernel_tables", _c_int, [_c_void_p, _c_void_p, _c_void_p]),
     ("tdg_kernel_entry_host", _c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_int,
                                        ctypes.POINTER(_c_double)]),
+    ("tdg_solve_forces_noalloc", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_set_pass_events", _c_int, [_c_void_p, ctypes.POINTER(_c_void_p), _c_int]),
     ("tdg_plan_info", _c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
