@@ -138,11 +138,15 @@ class Clocks:
 # algorithmic bytes per pass (FP32: 4-byte reals, 8-byte complex)
 # ------------------------------------------------------------------------------------------
 
-def pass_bytes(nx, ny, px, real):
-    hy = ny + 1 if px else ny + 1
+def pass_bytes(nx, ny, px, real, path):
+    """Compulsory bytes of each pass: every array it must read or write once, spectra as the
+    kernel path stores them (generic: both full spectra, P_x reals per frequency column;
+    register path: half spectra, nx + 4 reals per column)."""
+    hy = ny + 1
     cplx = 2 * real
+    spec = 2 * hy * px * real if path == 0 else hy * (nx + 4) * 2 * real
     a = nx * ny * real + nx * hy * cplx                        # sigma in, Z out
-    b = nx * hy * cplx + 2 * hy * px * real + 2 * nx * hy * cplx  # Z in, two spectra, G_x G_y out
+    b = nx * hy * cplx + spec + 2 * nx * hy * cplx             # Z in, spectra, G_x G_y out
     c = 2 * nx * hy * cplx + 2 * nx * ny * real                # G_x G_y in, F^x F^y out
     return {"rows_r2c": a, "cols_conv": b, "rows_c2r": c}
 
@@ -225,6 +229,7 @@ def time_form(form, sigma_host, n, K, W, world, rank, clocks=None):
     out = (h_fx.numpy().astype(np.float64), h_fy.numpy().astype(np.float64))
     info = plan.info()
     res = {"ms": ms, "per_pass_ms": per_pass, "e2e_ms": e2e_ms, "clocks": clk, "px": info["px"],
+           "path": plan.path(),
            "real": 8 if form == "fp64" else 4, "h2d": sigma.numel() * sigma.element_size(),
            "d2h": 2 * sigma.numel() * sigma.element_size(), "device_error": plan.device_error()}
     plan.close()
@@ -278,7 +283,7 @@ def run_ours(args):
     # roofline of the dominant kernel (largest share of the step)
     pk = peaks()
     dom = max(r["per_pass_ms"], key=r["per_pass_ms"].get)
-    algo = pass_bytes(n, n, r["px"], r["real"])[dom]
+    algo = pass_bytes(n, n, r["px"], r["real"], r["path"])[dom]
     achieved = algo / (r["per_pass_ms"][dom] * 1e-3) / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
     line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
@@ -286,7 +291,8 @@ def run_ours(args):
                         "peak_source": "measured" if pk else "fallback",
                         "algorithmic_bytes": algo,
                         "pass_ms": {k: round(v, 4) for k, v in r["per_pass_ms"].items()},
-                        "step_bytes": sum(pass_bytes(n, n, r["px"], r["real"]).values())}
+                        "step_bytes": sum(pass_bytes(n, n, r["px"], r["real"], r["path"]).values()),
+                        "kernel_path": "register" if r["path"] == 1 else "generic"}
     line["e2e"] = {"value": round(world * pts / (r["e2e_ms"] * 1e-3) / 1e6, 1), "unit": "Mpts/s",
                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
     line["gpu_launches"] = 3 * args.steps

@@ -65,6 +65,10 @@ class Plan:
                     ctypes.byref(prec))
         return {"px": px.value, "py": py.value, "order": order.value, "precision": prec.value}
 
+    def path(self) -> int:
+        """0: generic kernels, 1: FP32 register-transform kernels."""
+        return int(native.load().tdg_plan_path(self._h))
+
     def workspace_bytes(self) -> int:
         return int(native.load().tdg_workspace_bytes(self._h))
 

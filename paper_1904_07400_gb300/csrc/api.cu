@@ -136,10 +136,11 @@ void free_plan_memory(Plan& p) {
     cudaFree(p.tw_x);
     cudaFree(p.tw_y);
     cudaFree(p.spec);
+    cudaFree(p.spec_half);
     cudaFree(p.wq);
     cudaFree(p.err);
     if (p.work_owned) cudaFree(p.work);
-    p.tw_x = p.tw_y = p.spec = nullptr;
+    p.tw_x = p.tw_y = p.spec = p.spec_half = nullptr;
     p.wq = nullptr;
     p.err = nullptr;
     p.work = nullptr;
@@ -295,6 +296,10 @@ tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
         TDG_TRY(launch_spectra<double>(p, placed_x, placed_y, scratch, reinterpret_cast<double*>(p.spec), s));
     else
         TDG_TRY(launch_spectra<float>(p, placed_x, placed_y, scratch, reinterpret_cast<float*>(p.spec), s));
+    if (fast_fp32_eligible(p)) {
+        TDG_TRY(cudaMalloc(&p.spec_half, fast_fp32_spec_bytes(p)));
+        TDG_TRY(launch_half_spectra(p, s));
+    }
     TDG_TRY(cudaStreamSynchronize(s));
     cudaFree(placed_x);
     cudaFree(placed_y);
@@ -440,6 +445,11 @@ tdg_status tdg_plan_info(const tdg_plan h, int* px, int* py, int* order, int* pr
     if (order) *order = h->p.order;
     if (precision) *precision = (int)h->p.prec;
     return TDG_OK;
+}
+
+int tdg_plan_path(const tdg_plan h) {
+    if (!h) return -1;
+    return (h->p.spec_half && fast_fp32_eligible(h->p)) ? 1 : 0;
 }
 
 tdg_status tdg_destroy(tdg_plan h) {

@@ -1,0 +1,419 @@
+// FP32 force solve for grids whose sides are 1024, 2048 or 4096 cells: the same three
+// passes as solve_kernels.cu, with register-resident transforms (fft_reg.cuh) and two
+// structural savings:
+//
+//  * Zero padding used exactly.  The column transform of length 2N of a column whose upper
+//    half is zero splits into two transforms of length N: even frequencies
+//    X_e = FFT_N(x), odd frequencies X_o = FFT_N(x_n W_2N^n).  The inverse, cropped to the
+//    first N rows, splits the same way: y = IFFT_N(Y_e) + W_2N^-n IFFT_N(Y_o).  Nothing of
+//    length 2N is ever formed.
+//  * Half spectra.  For fixed ky, s_x is odd and s_y even in kx, so each of the even and odd
+//    half-tables is (anti)symmetric about its middle; only the first half of each is stored
+//    (8 bytes per output point for both spectra together).
+//
+// Intermediates use two-column tiles: element (row i, frequency ky) of an nx x hy complex
+// array lives at [ky / 2][i][ky % 2], so a column-pass block reads and writes contiguous
+// nx x 16-byte slabs.
+#include <cuda_runtime.h>
+
+#include "fft_reg.cuh"
+#include "tdg_internal.cuh"
+
+namespace tdg {
+namespace {
+
+using reg::cf;
+using reg::pad;
+
+constexpr int kTW = 2;  // tile width of the intermediates
+
+// ---------------------------------------------------------------------------------------
+// truncated tridiagonal solve (1/8)(c_{i-1} + 6 c_i + c_{i+1}) = s_i on one line held in
+// shared memory (element i at idx(i)); tpl threads per line, thread t owns a contiguous
+// chunk and starts its recurrences W steps early from zero (error lam^W, lam = 3 - 2 sqrt 2)
+// ---------------------------------------------------------------------------------------
+constexpr int kLam = 32;
+constexpr int kWarm = 12;
+
+__device__ __forceinline__ void fill_lambda(float* lam) {
+    if (threadIdx.x == 0) {
+        double d = 6.0;
+        for (int i = 0; i < kLam; ++i) {
+            lam[i] = (float)(1.0 / d);
+            d = 6.0 - 1.0 / d;
+        }
+    }
+}
+
+__device__ __forceinline__ float vs(float a, float s) { return a * s; }
+__device__ __forceinline__ cf vs(cf a, float s) { return scl(a, s); }
+
+template <typename V, bool PAD>
+__device__ __forceinline__ int ix(int i) { return PAD ? pad(i) : i; }
+
+// all threads of the block call this (it synchronises); each line handled by tpl threads
+template <typename V, bool PAD>
+__device__ void solve_line(const V* src, V* tmp, V* dst, int n, int t, int tpl, const float* lam) {
+    const float linf = lam[kLam - 1];
+    const int chunk = (n + tpl - 1) / tpl;
+    const int a = t * chunk;
+    const int b = min(n, a + chunk);
+    if (a < n) {
+        int s0 = a - kWarm;
+        V y;
+        int start;
+        if (s0 < kLam) {
+            y = vs(src[ix<V, PAD>(0)], 8.0f);
+            if (a == 0) tmp[ix<V, PAD>(0)] = y;
+            start = 1;
+        } else {
+            y = vs(src[ix<V, PAD>(0)], 0.0f);
+            start = s0;
+        }
+        for (int i = start; i < b; ++i) {
+            float l = (i - 1 < kLam) ? lam[i - 1] : linf;
+            y = vs(src[ix<V, PAD>(i)], 8.0f) - vs(y, l);
+            if (i >= a) tmp[ix<V, PAD>(i)] = y;
+        }
+    }
+    __syncthreads();
+    if (a < n) {
+        int e0 = b - 1 + kWarm;
+        V c;
+        int i0;
+        if (e0 >= n - 1) {
+            i0 = n - 1;
+            float l = (i0 < kLam) ? lam[i0] : linf;
+            c = vs(tmp[ix<V, PAD>(i0)], l);
+            if (i0 < b) dst[ix<V, PAD>(i0)] = c;
+            --i0;
+        } else {
+            i0 = e0;
+            c = vs(tmp[ix<V, PAD>(0)], 0.0f);
+        }
+        for (int i = i0; i >= a; --i) {
+            float l = (i < kLam) ? lam[i] : linf;
+            c = vs(tmp[ix<V, PAD>(i)] - c, l);
+            if (i < b) dst[ix<V, PAD>(i)] = c;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ cf ld2(const cf* p) {
+    float2 v = *reinterpret_cast<const float2*>(p);
+    return mk(v.x, v.y);
+}
+
+// X = (Za + conj Zb)/2 - i w (Za - conj Zb)/2
+__device__ __forceinline__ cf unpack_r2c(cf za, cf zb, cf w) {
+    cf e = mk(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+    cf d = mk(0.5f * (za.x - zb.x), 0.5f * (za.y + zb.y));
+    cf wd = cmul(w, d);
+    return mk(e.x + wd.y, e.y - wd.x);
+}
+
+// Z = (Xa + conj Xb) + i conj(w) (Xa - conj Xb)
+__device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
+    cf e = mk(xa.x + xb.x, xa.y - xb.y);
+    cf d = mk(xa.x - xb.x, xa.y + xb.y);
+    cf wd = cmulc(d, w);
+    return mk(e.x - wd.y, e.y + wd.x);
+}
+
+// ---------------------------------------------------------------------------------------
+// pass A: one row per block (T = L / 16 threads), row length L = ny (packed complex length
+// L, period 2L).  Several blocks share an SM, so one block's barrier waits overlap with
+// another's work.
+// ---------------------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict__ sigma, int nx, int solve,
+                                                         const cf* __restrict__ tw, cf* __restrict__ z) {
+    constexpr int T = L / 16;
+    constexpr int R1 = reg::Mid<L>::R1;
+    constexpr int LP = L + L / 16 + 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cf* eb = reinterpret_cast<cf*>(smem_raw);                 // LP
+    float* rbuf = reinterpret_cast<float*>(eb + LP);          // LP floats (order 3 only)
+    float* lam = rbuf + LP;
+    const int t = threadIdx.x;
+    const int i = blockIdx.x;
+    cf v[16];
+    if (solve) {
+        // row into shared memory with one pad word per 16 (the solve's per-thread chunks
+        // of 16 then fall in distinct banks)
+        const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * L);
+        for (int q = t; q < L / 4; q += T) {
+            float4 x = src[q];
+            int e = 4 * q;
+            float* d = rbuf + pad(e);
+            d[0] = x.x;
+            d[1] = x.y;
+            d[2] = x.z;
+            d[3] = x.w;
+        }
+        fill_lambda(lam);
+        __syncthreads();
+        solve_line<float, true>(rbuf, reinterpret_cast<float*>(eb), rbuf, L, t, T, lam);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            int n = t + r * T;
+            v[r] = mk(rbuf[pad(2 * n)], rbuf[pad(2 * n + 1)]);
+        }
+    } else {
+        const float2* row = reinterpret_cast<const float2*>(sigma + (size_t)i * L);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            float2 x = row[t + r * T];
+            v[r] = mk(x.x, x.y);
+        }
+    }
+#pragma unroll
+    for (int r = 8; r < 16; ++r) v[r] = mk(0.f, 0.f);
+    reg::fft<L, R1, 2>(v, eb, tw, t);
+    // unpack the real transform: X[k] from Z[k] and Z[L - k]
+#pragma unroll
+    for (int r = 0; r < 16; ++r) eb[pad(t + r * T)] = v[r];
+    __syncthreads();
+    const size_t slab = (size_t)nx * kTW;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int k = t + r * T;
+        cf zb = eb[pad((L - k) & (L - 1))];
+        z[(size_t)(k >> 1) * slab + (size_t)i * kTW + (k & 1)] = unpack_r2c(v[r], zb, reg::ld_tw(tw, k));
+    }
+    if (t == 0) z[(size_t)(L >> 1) * slab + (size_t)i * kTW] = mk(v[0].x - v[0].y, 0.f);
+}
+
+// ---------------------------------------------------------------------------------------
+// pass B: one column ky per block, column length L = nx
+// spec: per ky, the even half (L/2 + 1 values, padded to HS) then the odd half (L/2), each
+// value (s_x, s_y) already scaled by G / (P_x P_y)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 ld_spec(const float2* p) { return __ldg(p); }
+
+// i s X for the even (H = 0) or odd (H = 1) half, component comp, at k = t + r T
+template <int L, int H>
+__device__ __forceinline__ void spec_product(cf* w, const cf* v, const float2* sh, int comp, int t) {
+    constexpr int T = L / 16;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int k = t + r * T;
+        float s;
+        bool direct = H == 0 ? (r < 8 || (r == 8 && t == 0)) : (r < 8);
+        if (direct) {
+            float2 q = ld_spec(sh + k);
+            s = comp ? q.y : q.x;
+        } else {
+            float2 q = ld_spec(sh + (H == 0 ? L - k : L - 1 - k));
+            s = comp ? q.y : -q.x;  // s_x odd, s_y even about the middle of the half
+        }
+        w[r] = mk(-s * v[r].y, s * v[r].x);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(L / 16, 2) k_fast_cols(const cf* __restrict__ z, int hy, int solve,
+                                                         const cf* __restrict__ tw,
+                                                         const float2* __restrict__ spec, cf* __restrict__ gx,
+                                                         cf* __restrict__ gy) {
+    constexpr int T = L / 16;
+    constexpr int R1 = reg::Mid<L>::R1;
+    constexpr int LP = L + L / 16 + 16;
+    constexpr int HS = L / 2 + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cf* xb = reinterpret_cast<cf*>(smem_raw);   // LP: the column, later the even-half result
+    cf* eb = xb + LP;                            // LP: transform exchanges, solve scratch
+    float* lam = reinterpret_cast<float*>(eb + LP);
+    const int t = threadIdx.x;
+    const int ky = blockIdx.x;
+    const int tile = ky >> 1, c = ky & 1;
+    const size_t slab = (size_t)L * kTW;
+    const cf* zc = z + (size_t)tile * slab + c;
+    for (int i = t; i < L; i += T) xb[pad(i)] = zc[(size_t)i * kTW];
+    if (solve) fill_lambda(lam);
+    __syncthreads();
+    if (solve) solve_line<cf, true>(xb, eb, xb, L, t, T, lam);
+
+    cf v[16], u[16], w[16];
+    // even and odd frequency halves of the padded column transform
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int n = t + r * T;
+        cf x = xb[pad(n)];
+        v[r] = x;
+        u[r] = cmul(x, reg::ld_tw(tw, n));  // twist by W_2L^n
+    }
+    reg::fft<L, R1, 2>(v, eb, tw, t);
+    reg::fft<L, R1, 2>(u, eb, tw, t);
+    const float2* se = spec + (size_t)ky * 2 * HS;
+    const float2* so = se + HS;
+    cf* g[2] = {gx + (size_t)tile * slab + c, gy + (size_t)tile * slab + c};
+#pragma unroll
+    for (int comp = 0; comp < 2; ++comp) {
+        spec_product<L, 0>(w, v, se, comp, t);
+        reg::ifft<L, R1, 2>(w, eb, tw, t);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = w[r];  // own positions only
+        spec_product<L, 1>(w, u, so, comp, t);
+        reg::ifft<L, R1, 2>(w, eb, tw, t);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            int n = t + r * T;
+            g[comp][(size_t)n * kTW] = xb[pad(n)] + cmulc(w[r], reg::ld_tw(tw, n));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// pass C: one row of one component per block (blockIdx.y = component)
+// ---------------------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restrict__ g0,
+                                                             const cf* __restrict__ g1, int nx,
+                                                             const cf* __restrict__ tw, float* __restrict__ f0,
+                                                             float* __restrict__ f1) {
+    constexpr int T = L / 16;
+    constexpr int R1 = reg::Mid<L>::R1;
+    constexpr int LP = L + L / 16 + 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cf* xb = reinterpret_cast<cf*>(smem_raw);  // LP
+    const cf* g = blockIdx.y ? g1 : g0;
+    float* f = blockIdx.y ? f1 : f0;
+    const int t = threadIdx.x;
+    const int i = blockIdx.x;
+    const size_t slab = (size_t)nx * kTW;
+    // X[k], k = 0..L (the tile pair (2p, 2p + 1) of row i is one 16-byte word)
+    for (int p = t; p <= L / 2; p += T) {
+        float4 d = *reinterpret_cast<const float4*>(g + (size_t)p * slab + (size_t)i * kTW);
+        xb[pad(2 * p)] = mk(d.x, d.y);
+        xb[pad(2 * p + 1)] = mk(d.z, d.w);
+    }
+    __syncthreads();
+    cf v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int k = t + r * T;
+        v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::ld_tw(tw, k));
+    }
+    __syncthreads();
+    reg::ifft<L, R1, 2>(v, xb, tw, t);
+    float2* out = reinterpret_cast<float2*>(f + (size_t)i * L);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) out[t + r * T] = make_float2(v[r].x, v[r].y);
+}
+
+// spectra in the half layout from the full FP32 spectra [c][ky][kx]
+__global__ void k_half_spectra(const float* __restrict__ full, int hy, int Px, float2* __restrict__ half) {
+    const int L = Px / 2;
+    const int HS = L / 2 + 2;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = (long)hy * 2 * HS;
+    if (idx >= total) return;
+    int ky = (int)(idx / (2 * HS));
+    int rem = (int)(idx % (2 * HS));
+    int h = rem / HS, k = rem % HS;
+    int kx = 2 * k + h;
+    float2 v = make_float2(0.f, 0.f);
+    bool ok = (h == 0) ? (k <= L / 2) : (k < L / 2);
+    if (ok) {
+        v.x = full[(size_t)ky * Px + kx];
+        v.y = full[(size_t)hy * Px + (size_t)ky * Px + kx];
+    }
+    half[idx] = v;
+}
+
+template <int L>
+size_t rows_smem(int solve) {
+    constexpr int LP = L + L / 16 + 16;
+    return LP * sizeof(cf) + (solve ? LP * sizeof(float) : 0) + kLam * sizeof(float);
+}
+
+template <int L>
+size_t cols_smem() {
+    constexpr int LP = L + L / 16 + 16;
+    return 2 * LP * sizeof(cf) + kLam * sizeof(float);
+}
+
+template <int L>
+size_t inv_smem() {
+    constexpr int LP = L + L / 16 + 16;
+    return LP * sizeof(cf);
+}
+
+template <int LX, int LY>
+cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+    const int hy = p.hy;
+    const int ntile = (hy + kTW - 1) / kTW;
+    const size_t n_el = (size_t)ntile * p.nx * kTW;
+    cf* z = reinterpret_cast<cf*>(work);
+    cf* gx = z + n_el;
+    cf* gy = gx + n_el;
+    const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
+    const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
+    const int solve = p.order == 3;
+    cudaError_t e;
+    size_t sm = rows_smem<LY>(solve);
+    if ((e = cudaFuncSetAttribute(k_fast_rows<LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+        return e;
+    mark(p, 0, s);
+    k_fast_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, p.nx, solve, twy, z);
+    if ((e = cudaGetLastError())) return e;
+    mark(p, 1, s);
+    sm = cols_smem<LX>();
+    if ((e = cudaFuncSetAttribute(k_fast_cols<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+        return e;
+    k_fast_cols<LX><<<hy, LX / 16, sm, s>>>(z, hy, solve, twx, reinterpret_cast<const float2*>(p.spec_half), gx,
+                                             gy);
+    if ((e = cudaGetLastError())) return e;
+    mark(p, 2, s);
+    sm = inv_smem<LY>();
+    if ((e = cudaFuncSetAttribute(k_fast_rows_inv<LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+        return e;
+    dim3 grid(p.nx, 2);
+    k_fast_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gx, gy, p.nx, twy, fx, fy);
+    e = cudaGetLastError();
+    mark(p, 3, s);
+    return e;
+}
+
+template <int LX>
+cudaError_t run_fast_x(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+    switch (p.ny) {
+        case 1024: return run_fast<LX, 1024>(p, sigma, fx, fy, work, s);
+        case 2048: return run_fast<LX, 2048>(p, sigma, fx, fy, work, s);
+        default: return run_fast<LX, 4096>(p, sigma, fx, fy, work, s);
+    }
+}
+
+bool fast_side(int n) { return n == 1024 || n == 2048 || n == 4096; }
+
+}  // namespace
+
+bool fast_fp32_eligible(const Plan& p) {
+    return p.prec != TDG_FP64 && fast_side(p.nx) && fast_side(p.ny) && p.ax.P == 2 * p.nx && p.ay.P == 2 * p.ny;
+}
+
+size_t fast_fp32_spec_bytes(const Plan& p) {
+    const int HS = p.nx / 2 + 2;
+    return (size_t)p.hy * 2 * HS * sizeof(float2);
+}
+
+cudaError_t launch_half_spectra(const Plan& p, cudaStream_t s) {
+    const int HS = p.nx / 2 + 2;
+    long total = (long)p.hy * 2 * HS;
+    k_half_spectra<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float*>(p.spec), p.hy,
+                                                                    p.ax.P, reinterpret_cast<float2*>(p.spec_half));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
+                                cudaStream_t s) {
+    switch (p.nx) {
+        case 1024: return run_fast_x<1024>(p, sigma, fx, fy, work, s);
+        case 2048: return run_fast_x<2048>(p, sigma, fx, fy, work, s);
+        default: return run_fast_x<4096>(p, sigma, fx, fy, work, s);
+    }
+}
+
+}  // namespace tdg

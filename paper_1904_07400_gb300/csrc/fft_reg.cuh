@@ -1,0 +1,194 @@
+// Register-resident FFT of one line of length L = 16 * R1 * 16 (R1 in {4, 8, 16}) by T =
+// L / 16 threads, 16 complex values per thread, two exchanges through padded shared memory.
+//
+// Data distribution at entry and exit: thread t holds element t + r * T in v[r], r < 16
+// ("natural strided").  Three Stockham stages (radix 16, R1, 16); the last stage leaves its
+// outputs exactly where the first stage of the next transform reads its inputs, so a
+// forward transform, a pointwise product and an inverse transform chain without any
+// reordering.  The inverse transform is conj(FFT(conj(x))).
+//
+// Shared buffer per line: L + L/16 complex values; element i lives at i + i/16 (the pad
+// spreads the stride-16 stores of the first stage over all banks).
+#pragma once
+
+#include "tdg_internal.cuh"
+
+namespace tdg {
+namespace reg {
+
+typedef cpx<float> cf;
+
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ cf ld_tw(const cf* tw, int i) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(tw) + i);
+    return mk(v.x, v.y);
+}
+
+__device__ __forceinline__ cf mul_w16(cf a, int q) {
+    // exp(-2 pi i q / 16)
+    const float c1 = 0.923879532511286756f, s1 = 0.382683432365089772f, h = 0.707106781186547524f;
+    switch (q & 15) {
+        case 0: return a;
+        case 1: return mk(a.x * c1 + a.y * s1, a.y * c1 - a.x * s1);
+        case 2: return mk(h * (a.x + a.y), h * (a.y - a.x));
+        case 3: return mk(a.x * s1 + a.y * c1, a.y * s1 - a.x * c1);
+        case 4: return mk(a.y, -a.x);
+        case 6: return mk(h * (a.y - a.x), -h * (a.x + a.y));
+        case 9: return mk(-a.x * c1 - a.y * s1, a.x * s1 - a.y * c1);
+        default: {
+            float sn, cs;
+            sincospif(-2.0f * (float)q / 16.0f, &sn, &cs);
+            return mk(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
+        }
+    }
+}
+
+__device__ __forceinline__ void dft2(cf& a, cf& b) {
+    cf t = a - b;
+    a = a + b;
+    b = t;
+}
+
+// forward DFT_4 in place on (a0, a1, a2, a3)
+__device__ __forceinline__ void dft4(cf& a0, cf& a1, cf& a2, cf& a3) {
+    cf t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = a1 - a3;
+    t3 = mk(t3.y, -t3.x);  // * (-i)
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = t1 + t3;
+    a3 = t1 - t3;
+}
+
+// forward DFT_8 in place on a[0..7] (stride s in the register array)
+template <int S>
+__device__ __forceinline__ void dft8(cf* a) {
+    cf e0 = a[0], e1 = a[2 * S], e2 = a[4 * S], e3 = a[6 * S];
+    cf o0 = a[S], o1 = a[3 * S], o2 = a[5 * S], o3 = a[7 * S];
+    dft4(e0, e1, e2, e3);
+    dft4(o0, o1, o2, o3);
+    o1 = mul_w16(o1, 2);
+    o2 = mul_w16(o2, 4);
+    o3 = mul_w16(o3, 6);
+    a[0] = e0 + o0;
+    a[4 * S] = e0 - o0;
+    a[S] = e1 + o1;
+    a[5 * S] = e1 - o1;
+    a[2 * S] = e2 + o2;
+    a[6 * S] = e2 - o2;
+    a[3 * S] = e3 + o3;
+    a[7 * S] = e3 - o3;
+}
+
+// forward DFT_16 in place on a[0..15]: n = 4 n1 + n2, k = k1 + 4 k2
+__device__ __forceinline__ void dft16(cf* a) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+    // now a[4 k1 + n2] = B[n2][k1]; twiddle W16^(n2 k1)
+    a[5] = mul_w16(a[5], 1);
+    a[6] = mul_w16(a[6], 2);
+    a[7] = mul_w16(a[7], 3);
+    a[9] = mul_w16(a[9], 2);
+    a[10] = mul_w16(a[10], 4);
+    a[11] = mul_w16(a[11], 6);
+    a[13] = mul_w16(a[13], 3);
+    a[14] = mul_w16(a[14], 6);
+    a[15] = mul_w16(a[15], 9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    // a[4 k1 + k2] = A[k1 + 4 k2]: transpose 4 x 4 into natural order
+    cf t;
+    t = a[1]; a[1] = a[4]; a[4] = t;
+    t = a[2]; a[2] = a[8]; a[8] = t;
+    t = a[3]; a[3] = a[12]; a[12] = t;
+    t = a[6]; a[6] = a[9]; a[9] = t;
+    t = a[7]; a[7] = a[13]; a[13] = t;
+    t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+// radix-R butterflies of one stage on the thread's 16 values; butterfly b uses
+// v[b * R .. b * R + R - 1] (element r at v[b * R + r])
+template <int R>
+__device__ __forceinline__ void butterflies(cf* v) {
+    if constexpr (R == 16) {
+        dft16(v);
+    } else if constexpr (R == 8) {
+        dft8<1>(v);
+        dft8<1>(v + 8);
+    } else {
+        dft4(v[0], v[1], v[2], v[3]);
+        dft4(v[4], v[5], v[6], v[7]);
+        dft4(v[8], v[9], v[10], v[11]);
+        dft4(v[12], v[13], v[14], v[15]);
+    }
+}
+
+// One exchange: registers (outputs of a stage of radix RA with stride NSA) -> shared ->
+// registers (inputs of the next stage of radix RB).  tw: W_L^m at tw[m * TS].
+template <int L, int RA, int NSA, int RB>
+__device__ __forceinline__ void exchange(cf* v, cf* buf, int t) {
+    constexpr int T = L / 16;
+    constexpr int BA = 16 / RA;
+#pragma unroll
+    for (int b = 0; b < BA; ++b) {
+        int j = t + T * b;
+        int base = (j / NSA) * NSA * RA + (j % NSA);
+#pragma unroll
+        for (int r = 0; r < RA; ++r) buf[pad(base + r * NSA)] = v[b * RA + r];
+    }
+    __syncthreads();
+    constexpr int BB = 16 / RB;
+#pragma unroll
+    for (int b = 0; b < BB; ++b) {
+        int j = t + T * b;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) v[b * RB + r] = buf[pad(j + r * (L / RB))];
+    }
+    __syncthreads();
+}
+
+// twiddles of a stage with radix R after NS elements have been combined:
+// element r of butterfly j times W_{NS R}^(r (j mod NS)) = W_L^(r k L / (NS R))
+template <int L, int R, int NS, int TS>
+__device__ __forceinline__ void twiddle(cf* v, const cf* tw, int t) {
+    constexpr int T = L / 16;
+    constexpr int B = 16 / R;
+    constexpr int STEP = L / (NS * R);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        int k = (t + T * b) % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], ld_tw(tw, r * k * STEP * TS));
+    }
+}
+
+// Forward FFT of length L = 16 * R1 * 16; v natural strided in and out.  buf: this line's
+// shared buffer (L + L/16 values).  tw: table with W_L^m at tw[m * TS].
+template <int L, int R1, int TS>
+__device__ __forceinline__ void fft(cf* v, cf* buf, const cf* tw, int t) {
+    static_assert(16 * R1 * 16 == L, "L = 16 * R1 * 16");
+    butterflies<16>(v);
+    exchange<L, 16, 1, R1>(v, buf, t);
+    twiddle<L, R1, 16, TS>(v, tw, t);
+    butterflies<R1>(v);
+    exchange<L, R1, 16, 16>(v, buf, t);
+    twiddle<L, 16, 16 * R1, TS>(v, tw, t);
+    butterflies<16>(v);
+}
+
+template <int L, int R1, int TS>
+__device__ __forceinline__ void ifft(cf* v, cf* buf, const cf* tw, int t) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
+    fft<L, R1, TS>(v, buf, tw, t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
+}
+
+template <int L> struct Mid;
+template <> struct Mid<1024> { static constexpr int R1 = 4; };
+template <> struct Mid<2048> { static constexpr int R1 = 8; };
+template <> struct Mid<4096> { static constexpr int R1 = 16; };
+
+}  // namespace reg
+}  // namespace tdg

@@ -39,6 +39,7 @@ SIGNATURES = [
     ("tdg_set_pass_events", _c_int, [_c_void_p, ctypes.POINTER(_c_void_p), _c_int]),
     ("tdg_plan_info", _c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    ("tdg_plan_path", _c_int, [_c_void_p]),
     ("tdg_destroy", _c_int, [_c_void_p]),
     ("tdg_status_string", ctypes.c_char_p, [_c_int]),
 ]
@@ -79,7 +80,7 @@ def call(name: str, *args):
     """Call one C entry point; raise TdgError on a non-OK status (status-returning calls)."""
     lib = load()
     res = getattr(lib, name)(*args)
-    if name not in ("tdg_workspace_bytes", "tdg_status_string"):
+    if name not in ("tdg_workspace_bytes", "tdg_status_string", "tdg_plan_path"):
         check(name, res)
     return res
 

@@ -1,0 +1,64 @@
+"""Parity of the FP32 register-transform path (sides of 1024, 2048, 4096 cells).
+
+The FP32 form of these grids runs the fast kernels; the FP64 form runs the generic ones,
+so the comparison also cross-checks two independent kernel sets.  Tolerance: FP32
+relative L2 <= 1e-5 against the FP64 oracle (and against the FP64 GPU form, itself within
+1e-12 of the oracle).
+"""
+import numpy as np
+import pytest
+
+from gpu_common import TOL_FP32, library, oracle_solver, rel_l2_pair, to_np
+from workloads import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    library()
+
+
+def _forces(nx, ny, k, dx, dy, prec, sigma):
+    import torch
+    from paper_1904_07400_gb300.api import Plan
+    p = Plan(nx, ny, k, dx, dy, precision=prec)
+    s = torch.as_tensor(sigma, dtype=p.dtype, device=p.device)
+    fx, fy = p.forces(s)
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    return to_np(fx), to_np(fy)
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024), (1024, 2048), (2048, 1024), (4096, 1024), (1024, 4096)])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fast_path_vs_fp64_gpu(shape, k):
+    nx, ny = shape
+    dx, dy = 1.0 / nx, 1.0 / ny
+    sigma = syn.clumps(nx, ny, seed=nx + 7 * ny + k)
+    f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
+    f64 = _forces(nx, ny, k, dx, dy, "fp64", sigma)
+    assert rel_l2_pair(*f32, *f64) <= TOL_FP32
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_fast_path_vs_oracle_nonsquare_cells(k):
+    nx, ny = 1024, 2048
+    dx, dy = 1.0 / 1024, 0.7 / 2048
+    rng = np.random.default_rng(k)
+    sigma = syn.clumps(nx, ny, seed=k) + 0.1 * rng.random((nx, ny))
+    rx, ry = oracle_solver(nx, ny, k, dx, dy).forces(sigma)
+    f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
+    assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
+
+
+def test_fast_path_edges_and_ragged_support():
+    # density touching every edge of the grid (the truncated spline solve and the zero
+    # padding both matter there), order 3, against the oracle
+    nx = ny = 1024
+    dx = 1.0 / nx
+    rng = np.random.default_rng(9)
+    sigma = rng.random((nx, ny))
+    rx, ry = oracle_solver(nx, ny, 3, dx, dx).forces(sigma)
+    f32 = _forces(nx, ny, 3, dx, dx, "fp32", sigma)
+    assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
