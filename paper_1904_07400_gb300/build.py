@@ -54,8 +54,9 @@ def _compile(src: str, extra: list[str]) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Build (if stale) and return the path of libtdgrav.so."""
-    extra = list(extra or [])
+    """Build (if stale) and return the path of libtdgrav.so.  `extra` adds nvcc flags
+    (for instance -D knobs); TDG_NVCC_EXTRA in the environment does the same."""
+    extra = list(extra or []) + os.environ.get("TDG_NVCC_EXTRA", "").split()
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

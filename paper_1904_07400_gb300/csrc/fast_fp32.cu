@@ -176,11 +176,12 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
     for (int r = 0; r < 16; ++r) eb[pad(t + r * T)] = v[r];
     __syncthreads();
     const size_t slab = (size_t)nx * kTW;
+    const cf wt = reg::ld_tw(tw, t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int k = t + r * T;
         cf zb = eb[pad((L - k) & (L - 1))];
-        z[(size_t)(k >> 1) * slab + (size_t)i * kTW + (k & 1)] = unpack_r2c(v[r], zb, reg::ld_tw(tw, k));
+        z[(size_t)(k >> 1) * slab + (size_t)i * kTW + (k & 1)] = unpack_r2c(v[r], zb, reg::twist(wt, r));
     }
     if (t == 0) z[(size_t)(L >> 1) * slab + (size_t)i * kTW] = mk(v[0].x - v[0].y, 0.f);
 }
@@ -192,28 +193,31 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 ld_spec(const float2* p) { return __ldg(p); }
 
-// i s X for the even (H = 0) or odd (H = 1) half, component comp, at k = t + r T
+// (i s_x X, i s_y X) for the even (H = 0) or odd (H = 1) half at k = t + r T: wx gets the
+// x product, v is overwritten with the y product (one load of each spectrum value)
 template <int L, int H>
-__device__ __forceinline__ void spec_product(cf* w, const cf* v, const float2* sh, int comp, int t) {
+__device__ __forceinline__ void spec_products(cf* wx, cf* v, const float2* sh, int t) {
     constexpr int T = L / 16;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int k = t + r * T;
-        float s;
         bool direct = H == 0 ? (r < 8 || (r == 8 && t == 0)) : (r < 8);
-        if (direct) {
-            float2 q = ld_spec(sh + k);
-            s = comp ? q.y : q.x;
-        } else {
-            float2 q = ld_spec(sh + (H == 0 ? L - k : L - 1 - k));
-            s = comp ? q.y : -q.x;  // s_x odd, s_y even about the middle of the half
-        }
-        w[r] = mk(-s * v[r].y, s * v[r].x);
+        float2 q = ld_spec(sh + (direct ? k : (H == 0 ? L - k : L - 1 - k)));
+        float sx = direct ? q.x : -q.x;  // s_x odd, s_y even about the middle of the half
+        float sy = q.y;
+        cf x = v[r];
+        wx[r] = mk(-sx * x.y, sx * x.x);
+        v[r] = mk(-sy * x.y, sy * x.x);
     }
 }
 
+// blocks per SM the column kernel is compiled for (register budget 65536 / (blocks * L/16))
+#ifndef TDG_COLS_BLOCKS
+#define TDG_COLS_BLOCKS 2
+#endif
+
 template <int L>
-__global__ void __launch_bounds__(L / 16, 2) k_fast_cols(const cf* __restrict__ z, int hy, int solve,
+__global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf* __restrict__ z, int hy, int solve,
                                                          const cf* __restrict__ tw,
                                                          const float2* __restrict__ spec, cf* __restrict__ gx,
                                                          cf* __restrict__ gy) {
@@ -222,9 +226,10 @@ __global__ void __launch_bounds__(L / 16, 2) k_fast_cols(const cf* __restrict__ 
     constexpr int LP = L + L / 16 + 16;
     constexpr int HS = L / 2 + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cf* xb = reinterpret_cast<cf*>(smem_raw);   // LP: the column, later the even-half result
+    cf* xb = reinterpret_cast<cf*>(smem_raw);   // LP: the column, later the even-half y result
     cf* eb = xb + LP;                            // LP: transform exchanges, solve scratch
-    float* lam = reinterpret_cast<float*>(eb + LP);
+    cf* sb = eb + LP;                            // LP: the even-half x result
+    float* lam = reinterpret_cast<float*>(sb + LP);
     const int t = threadIdx.x;
     const int ky = blockIdx.x;
     const int tile = ky >> 1, c = ky & 1;
@@ -235,33 +240,43 @@ __global__ void __launch_bounds__(L / 16, 2) k_fast_cols(const cf* __restrict__ 
     __syncthreads();
     if (solve) solve_line<cf, true>(xb, eb, xb, L, t, T, lam);
 
-    cf v[16], u[16], w[16];
-    // even and odd frequency halves of the padded column transform
+    const float2* se = spec + (size_t)ky * 2 * HS;
+    const float2* so = se + HS;
+    const cf wt = reg::ld_tw(tw, t);
+    cf v[16], w[16];
+    // even frequencies: X_e = FFT_N(x); both products; both inverse transforms
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
+    reg::fft<L, R1, 2>(v, eb, tw, t);
+    spec_products<L, 0>(w, v, se, t);
+    reg::ifft<L, R1, 2>(w, eb, tw, t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sb[pad(t + r * T)] = w[r];  // own positions only
+    reg::ifft<L, R1, 2>(v, eb, tw, t);
+    // odd frequencies: read the twisted column, then park the even y result in its place
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int n = t + r * T;
-        cf x = xb[pad(n)];
-        v[r] = x;
-        u[r] = cmul(x, reg::ld_tw(tw, n));  // twist by W_2L^n
+        w[r] = cmul(xb[pad(n)], reg::twist(wt, r));  // x_n W_2L^n
+        xb[pad(n)] = v[r];
     }
-    reg::fft<L, R1, 2>(v, eb, tw, t);
-    reg::fft<L, R1, 2>(u, eb, tw, t);
-    const float2* se = spec + (size_t)ky * 2 * HS;
-    const float2* so = se + HS;
-    cf* g[2] = {gx + (size_t)tile * slab + c, gy + (size_t)tile * slab + c};
+    reg::fft<L, R1, 2>(w, eb, tw, t);
 #pragma unroll
-    for (int comp = 0; comp < 2; ++comp) {
-        spec_product<L, 0>(w, v, se, comp, t);
-        reg::ifft<L, R1, 2>(w, eb, tw, t);
+    for (int r = 0; r < 16; ++r) v[r] = w[r];
+    spec_products<L, 1>(w, v, so, t);
+    reg::ifft<L, R1, 2>(w, eb, tw, t);
+    cf* gxc = gx + (size_t)tile * slab + c;
+    cf* gyc = gy + (size_t)tile * slab + c;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = w[r];  // own positions only
-        spec_product<L, 1>(w, u, so, comp, t);
-        reg::ifft<L, R1, 2>(w, eb, tw, t);
+    for (int r = 0; r < 16; ++r) {
+        int n = t + r * T;
+        gxc[(size_t)n * kTW] = sb[pad(n)] + cmulc(w[r], reg::twist(wt, r));
+    }
+    reg::ifft<L, R1, 2>(v, eb, tw, t);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            int n = t + r * T;
-            g[comp][(size_t)n * kTW] = xb[pad(n)] + cmulc(w[r], reg::ld_tw(tw, n));
-        }
+    for (int r = 0; r < 16; ++r) {
+        int n = t + r * T;
+        gyc[(size_t)n * kTW] = xb[pad(n)] + cmulc(v[r], reg::twist(wt, r));
     }
 }
 
@@ -291,10 +306,11 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restric
     }
     __syncthreads();
     cf v[16];
+    const cf wt = reg::ld_tw(tw, t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int k = t + r * T;
-        v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::ld_tw(tw, k));
+        v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::twist(wt, r));
     }
     __syncthreads();
     reg::ifft<L, R1, 2>(v, xb, tw, t);
@@ -332,7 +348,7 @@ size_t rows_smem(int solve) {
 template <int L>
 size_t cols_smem() {
     constexpr int LP = L + L / 16 + 16;
-    return 2 * LP * sizeof(cf) + kLam * sizeof(float);
+    return 3 * LP * sizeof(cf) + kLam * sizeof(float);
 }
 
 template <int L>

@@ -147,6 +147,81 @@ __device__ __forceinline__ void exchange(cf* v, cf* buf, int t) {
     __syncthreads();
 }
 
+// exp(-2 pi i r / 32), r < 32: the factors W_2L^(r T) = W_32^r of the per-element twists
+struct W32 {
+    float c, s;
+};
+__device__ __forceinline__ cf w32(int r) {
+    constexpr W32 tab[32] = {
+    {1.00000000000000000e+00f, -0.00000000000000000e+00f},
+    {9.80785280403230431e-01f, -1.95090322016128248e-01f},
+    {9.23879532511286738e-01f, -3.82683432365089782e-01f},
+    {8.31469612302545236e-01f, -5.55570233019602178e-01f},
+    {7.07106781186547573e-01f, -7.07106781186547462e-01f},
+    {5.55570233019602289e-01f, -8.31469612302545236e-01f},
+    {3.82683432365089837e-01f, -9.23879532511286738e-01f},
+    {1.95090322016128331e-01f, -9.80785280403230431e-01f},
+    {6.12323399573676604e-17f, -1.00000000000000000e+00f},
+    {-1.95090322016128193e-01f, -9.80785280403230431e-01f},
+    {-3.82683432365089726e-01f, -9.23879532511286738e-01f},
+    {-5.55570233019601956e-01f, -8.31469612302545458e-01f},
+    {-7.07106781186547462e-01f, -7.07106781186547573e-01f},
+    {-8.31469612302545347e-01f, -5.55570233019602178e-01f},
+    {-9.23879532511286738e-01f, -3.82683432365089893e-01f},
+    {-9.80785280403230431e-01f, -1.95090322016128609e-01f},
+    {-1.00000000000000000e+00f, -1.22464679914735321e-16f},
+    {-9.80785280403230431e-01f, 1.95090322016128359e-01f},
+    {-9.23879532511286850e-01f, 3.82683432365089671e-01f},
+    {-8.31469612302545458e-01f, 5.55570233019601956e-01f},
+    {-7.07106781186547684e-01f, 7.07106781186547462e-01f},
+    {-5.55570233019602178e-01f, 8.31469612302545236e-01f},
+    {-3.82683432365090337e-01f, 9.23879532511286516e-01f},
+    {-1.95090322016128664e-01f, 9.80785280403230320e-01f},
+    {-1.83697019872102969e-16f, 1.00000000000000000e+00f},
+    {1.95090322016128304e-01f, 9.80785280403230431e-01f},
+    {3.82683432365090004e-01f, 9.23879532511286627e-01f},
+    {5.55570233019601845e-01f, 8.31469612302545458e-01f},
+    {7.07106781186547351e-01f, 7.07106781186547684e-01f},
+    {8.31469612302545236e-01f, 5.55570233019602178e-01f},
+    {9.23879532511286516e-01f, 3.82683432365090392e-01f},
+    {9.80785280403230320e-01f, 1.95090322016128720e-01f}
+    };
+    return mk(tab[r & 31].c, tab[r & 31].s);
+}
+
+// v[r] *= w^r for r < R, from the loaded w^1 (and w^4, w^8 for R >= 8): each power is at
+// most four chained products from a table entry and is applied as soon as it is formed,
+// so only a handful of factors are live at once
+template <int R>
+__device__ __forceinline__ void apply_powers(cf* v, cf w1, cf w4, cf w8) {
+    v[1] = cmul(v[1], w1);
+    if constexpr (R > 2) {
+        cf w2 = cmul(w1, w1);
+        cf w3 = cmul(w2, w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        if constexpr (R > 4) {
+            cf w5 = cmul(w4, w1);
+            cf w6 = cmul(w4, w2);
+            cf w7 = cmul(w4, w3);
+            v[4] = cmul(v[4], w4);
+            v[5] = cmul(v[5], w5);
+            v[6] = cmul(v[6], w6);
+            v[7] = cmul(v[7], w7);
+            if constexpr (R > 8) {
+                v[8] = cmul(v[8], w8);
+                v[9] = cmul(v[9], cmul(w8, w1));
+                v[10] = cmul(v[10], cmul(w8, w2));
+                v[11] = cmul(v[11], cmul(w8, w3));
+                v[12] = cmul(v[12], cmul(w8, w4));
+                v[13] = cmul(v[13], cmul(w8, w5));
+                v[14] = cmul(v[14], cmul(w8, w6));
+                v[15] = cmul(v[15], cmul(w8, w7));
+            }
+        }
+    }
+}
+
 // twiddles of a stage with radix R after NS elements have been combined:
 // element r of butterfly j times W_{NS R}^(r (j mod NS)) = W_L^(r k L / (NS R))
 template <int L, int R, int NS, int TS>
@@ -156,11 +231,17 @@ __device__ __forceinline__ void twiddle(cf* v, const cf* tw, int t) {
     constexpr int STEP = L / (NS * R);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        int k = (t + T * b) % NS;
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], ld_tw(tw, r * k * STEP * TS));
+        const int e = ((t + T * b) % NS) * STEP;  // exponent unit of this butterfly
+        cf w1 = ld_tw(tw, e * TS);
+        cf w4 = R > 4 ? ld_tw(tw, ((4 * e) % L) * TS) : w1;
+        cf w8 = R > 8 ? ld_tw(tw, ((8 * e) % L) * TS) : w1;
+        apply_powers<R>(v + b * R, w1, w4, w8);
     }
 }
+
+// W_2L^(t + r T) for r < 16, from the table entry W_2L^t (tw has W_2L^m at tw[m]) and the
+// constants W_2L^(r T) = W_32^r (T = L / 16)
+__device__ __forceinline__ cf twist(cf wt, int r) { return cmul(wt, w32(r)); }
 
 // Forward FFT of length L = 16 * R1 * 16; v natural strided in and out.  buf: this line's
 // shared buffer (L + L/16 values).  tw: table with W_L^m at tw[m * TS].
