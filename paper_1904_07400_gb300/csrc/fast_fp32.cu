@@ -100,6 +100,64 @@ __device__ void solve_line(const V* src, V* tmp, V* dst, int n, int t, int tpl, 
     __syncthreads();
 }
 
+// Same solve for a line of exactly CH * T elements with thread t owning [t CH, t CH + CH):
+// fully unrolled, and branch-free for every thread but the first, because
+// lam_i = 1/d_i equals its limit 3 - 2 sqrt 2 to float precision for i >= 6 (|d_i - d_inf|
+// shrinks by lam^2 ~ 0.03 per step).  Warm-up of W = 10 steps: lam^10 = 2e-8.
+constexpr int kWarmFast = 10;
+constexpr int kExactRows = 6;
+
+template <typename V, int CH>
+__device__ __forceinline__ void solve_line_fast(const V* src, V* tmp, V* dst, int n, int t, const float* lam) {
+    const float li = lam[kLam - 1];
+    const int a = t * CH;
+    // forward sweep y_i = 8 s_i - lam_{i-1} y_{i-1}
+    if (t == 0) {
+        V y = vs(src[pad(0)], 8.0f);
+        tmp[pad(0)] = y;
+#pragma unroll 4
+        for (int i = 1; i < CH; ++i) {
+            float l = i - 1 < kExactRows ? lam[i - 1] : li;
+            y = vs(src[pad(i)], 8.0f) - vs(y, l);
+            tmp[pad(i)] = y;
+        }
+    } else {
+        V y = vs(src[pad(a - kWarmFast)], 8.0f);
+#pragma unroll 4
+        for (int i = 1; i < kWarmFast; ++i) y = vs(src[pad(a - kWarmFast + i)], 8.0f) - vs(y, li);
+#pragma unroll 4
+        for (int i = 0; i < CH; ++i) {
+            y = vs(src[pad(a + i)], 8.0f) - vs(y, li);
+            tmp[pad(a + i)] = y;
+        }
+    }
+    __syncthreads();
+    // backward sweep c_i = lam_i (y_i - c_{i+1}), exact at the end of the line
+    const int b = a + CH;
+    V c;
+    if (b == n) {
+        c = vs(tmp[pad(n - 1)], li);
+        dst[pad(n - 1)] = c;
+#pragma unroll 4
+        for (int i = CH - 2; i >= 0; --i) {
+            float l = a + i < kExactRows ? lam[a + i] : li;
+            c = vs(tmp[pad(a + i)] - c, l);
+            dst[pad(a + i)] = c;
+        }
+    } else {
+        c = vs(tmp[pad(b + kWarmFast - 1)], li);
+#pragma unroll 4
+        for (int i = kWarmFast - 2; i >= 0; --i) c = vs(tmp[pad(b + i)] - c, li);
+#pragma unroll 4
+        for (int i = CH - 1; i >= 0; --i) {
+            float l = a + i < kExactRows ? lam[a + i] : li;
+            c = vs(tmp[pad(a + i)] - c, l);
+            dst[pad(a + i)] = c;
+        }
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ cf ld2(const cf* p) {
     float2 v = *reinterpret_cast<const float2*>(p);
     return mk(v.x, v.y);
@@ -138,6 +196,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
     float* lam = rbuf + LP;
     const int t = threadIdx.x;
     const int i = blockIdx.x;
+    const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
     cf v[16];
     if (solve) {
         // row into shared memory with one pad word per 16 (the solve's per-thread chunks
@@ -154,7 +213,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
         }
         fill_lambda(lam);
         __syncthreads();
-        solve_line<float, true>(rbuf, reinterpret_cast<float*>(eb), rbuf, L, t, T, lam);
+        solve_line_fast<float, 16>(rbuf, reinterpret_cast<float*>(eb), rbuf, L, t, lam);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             int n = t + r * T;
@@ -170,7 +229,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
     }
 #pragma unroll
     for (int r = 8; r < 16; ++r) v[r] = mk(0.f, 0.f);
-    reg::fft<L, R1, 2>(v, eb, tw, t);
+    reg::fft<L, R1>(v, eb, tb, t);
     // unpack the real transform: X[k] from Z[k] and Z[L - k]
 #pragma unroll
     for (int r = 0; r < 16; ++r) eb[pad(t + r * T)] = v[r];
@@ -215,6 +274,10 @@ __device__ __forceinline__ void spec_products(cf* wx, cf* v, const float2* sh, i
 #ifndef TDG_COLS_BLOCKS
 #define TDG_COLS_BLOCKS 2
 #endif
+// 1: one force component per column block (see k_fast_cols_split)
+#ifndef TDG_COLS_SPLIT
+#define TDG_COLS_SPLIT 0
+#endif
 
 template <int L>
 __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf* __restrict__ z, int hy, int solve,
@@ -235,10 +298,21 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
     const int tile = ky >> 1, c = ky & 1;
     const size_t slab = (size_t)L * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
+    // the column's half spectra are read only after the solve and the first transform:
+    // start moving them into L2 now (one bulk prefetch per half)
+    if (t == 0) {
+        const float2* sp = spec + (size_t)ky * 2 * HS;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp), "r"((unsigned)(HS * sizeof(float2)))
+                     : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp + HS),
+                     "r"((unsigned)(HS * sizeof(float2)))
+                     : "memory");
+    }
+    const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
     for (int i = t; i < L; i += T) xb[pad(i)] = zc[(size_t)i * kTW];
     if (solve) fill_lambda(lam);
     __syncthreads();
-    if (solve) solve_line<cf, true>(xb, eb, xb, L, t, T, lam);
+    if (solve) solve_line_fast<cf, 16>(xb, eb, xb, L, t, lam);
 
     const float2* se = spec + (size_t)ky * 2 * HS;
     const float2* so = se + HS;
@@ -247,12 +321,12 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
     // even frequencies: X_e = FFT_N(x); both products; both inverse transforms
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
-    reg::fft<L, R1, 2>(v, eb, tw, t);
+    reg::fft<L, R1>(v, eb, tb, t);
     spec_products<L, 0>(w, v, se, t);
-    reg::ifft<L, R1, 2>(w, eb, tw, t);
+    reg::ifft<L, R1>(w, eb, tb, t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) sb[pad(t + r * T)] = w[r];  // own positions only
-    reg::ifft<L, R1, 2>(v, eb, tw, t);
+    reg::ifft<L, R1>(v, eb, tb, t);
     // odd frequencies: read the twisted column, then park the even y result in its place
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -260,23 +334,89 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
         w[r] = cmul(xb[pad(n)], reg::twist(wt, r));  // x_n W_2L^n
         xb[pad(n)] = v[r];
     }
-    reg::fft<L, R1, 2>(w, eb, tw, t);
+    reg::fft<L, R1>(w, eb, tb, t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = w[r];
     spec_products<L, 1>(w, v, so, t);
-    reg::ifft<L, R1, 2>(w, eb, tw, t);
+    reg::ifft<L, R1>(w, eb, tb, t);
     cf* gxc = gx + (size_t)tile * slab + c;
     cf* gyc = gy + (size_t)tile * slab + c;
+    const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int n = t + r * T;
-        gxc[(size_t)n * kTW] = sb[pad(n)] + cmulc(w[r], reg::twist(wt, r));
+        gxc[(size_t)n * kTW] = sb[pad(n)] + cmul(w[r], reg::untwist(wtc, r));
     }
-    reg::ifft<L, R1, 2>(v, eb, tw, t);
+    reg::ifft<L, R1>(v, eb, tb, t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int n = t + r * T;
-        gyc[(size_t)n * kTW] = xb[pad(n)] + cmulc(v[r], reg::twist(wt, r));
+        gyc[(size_t)n * kTW] = xb[pad(n)] + cmul(v[r], reg::untwist(wtc, r));
+    }
+}
+
+// Variant with one force component per block (grid 2 hy, blockIdx.x = 2 ky + comp): four
+// transforms per block instead of six per column-pair of components, but a single
+// 16-element array live at a time (no register spills at two blocks per SM).
+template <int L, int H>
+__device__ __forceinline__ void spec_product_one(cf* v, const float2* sh, int comp, int t) {
+    constexpr int T = L / 16;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int k = t + r * T;
+        bool direct = H == 0 ? (r < 8 || (r == 8 && t == 0)) : (r < 8);
+        float2 q = ld_spec(sh + (direct ? k : (H == 0 ? L - k : L - 1 - k)));
+        float s = comp ? q.y : (direct ? q.x : -q.x);
+        cf x = v[r];
+        v[r] = mk(-s * x.y, s * x.x);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols_split(const cf* __restrict__ z, int hy, int solve,
+                                                               const cf* __restrict__ tw,
+                                                               const float2* __restrict__ spec,
+                                                               cf* __restrict__ gx, cf* __restrict__ gy) {
+    constexpr int T = L / 16;
+    constexpr int R1 = reg::Mid<L>::R1;
+    constexpr int LP = L + L / 16 + 16;
+    constexpr int HS = L / 2 + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cf* xb = reinterpret_cast<cf*>(smem_raw);   // LP: the column
+    cf* eb = xb + LP;                            // LP: exchanges, solve scratch
+    cf* sb = eb + LP;                            // LP: the even-half result
+    float* lam = reinterpret_cast<float*>(sb + LP);
+    const int t = threadIdx.x;
+    const int ky = blockIdx.x >> 1, comp = blockIdx.x & 1;
+    const int tile = ky >> 1, c = ky & 1;
+    const size_t slab = (size_t)L * kTW;
+    const cf* zc = z + (size_t)tile * slab + c;
+    const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
+    for (int i = t; i < L; i += T) xb[pad(i)] = zc[(size_t)i * kTW];
+    if (solve) fill_lambda(lam);
+    __syncthreads();
+    if (solve) solve_line_fast<cf, 16>(xb, eb, xb, L, t, lam);
+    const float2* se = spec + (size_t)ky * 2 * HS;
+    const cf wt = reg::ld_tw(tw, t);
+    cf v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
+    reg::fft<L, R1>(v, eb, tb, t);
+    spec_product_one<L, 0>(v, se, comp, t);
+    reg::ifft<L, R1>(v, eb, tb, t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sb[pad(t + r * T)] = v[r];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(xb[pad(t + r * T)], reg::twist(wt, r));
+    reg::fft<L, R1>(v, eb, tb, t);
+    spec_product_one<L, 1>(v, se + HS, comp, t);
+    reg::ifft<L, R1>(v, eb, tb, t);
+    cf* gc = (comp ? gy : gx) + (size_t)tile * slab + c;
+    const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int n = t + r * T;
+        gc[(size_t)n * kTW] = sb[pad(n)] + cmul(v[r], reg::untwist(wtc, r));
     }
 }
 
@@ -298,6 +438,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restric
     const int t = threadIdx.x;
     const int i = blockIdx.x;
     const size_t slab = (size_t)nx * kTW;
+    const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
     // X[k], k = 0..L (the tile pair (2p, 2p + 1) of row i is one 16-byte word)
     for (int p = t; p <= L / 2; p += T) {
         float4 d = *reinterpret_cast<const float4*>(g + (size_t)p * slab + (size_t)i * kTW);
@@ -313,7 +454,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restric
         v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::twist(wt, r));
     }
     __syncthreads();
-    reg::ifft<L, R1, 2>(v, xb, tw, t);
+    reg::ifft<L, R1>(v, xb, tb, t);
     float2* out = reinterpret_cast<float2*>(f + (size_t)i * L);
 #pragma unroll
     for (int r = 0; r < 8; ++r) out[t + r * T] = make_float2(v[r].x, v[r].y);
@@ -377,10 +518,17 @@ cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, vo
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_smem<LX>();
+#if TDG_COLS_SPLIT
+    if ((e = cudaFuncSetAttribute(k_fast_cols_split<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+        return e;
+    k_fast_cols_split<LX><<<2 * hy, LX / 16, sm, s>>>(z, hy, solve, twx,
+                                                       reinterpret_cast<const float2*>(p.spec_half), gx, gy);
+#else
     if ((e = cudaFuncSetAttribute(k_fast_cols<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
         return e;
     k_fast_cols<LX><<<hy, LX / 16, sm, s>>>(z, hy, solve, twx, reinterpret_cast<const float2*>(p.spec_half), gx,
                                              gy);
+#endif
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
     sm = inv_smem<LY>();

@@ -222,46 +222,63 @@ __device__ __forceinline__ void apply_powers(cf* v, cf w1, cf w4, cf w8) {
     }
 }
 
-// twiddles of a stage with radix R after NS elements have been combined:
-// element r of butterfly j times W_{NS R}^(r (j mod NS)) = W_L^(r k L / (NS R))
-template <int L, int R, int NS, int TS>
-__device__ __forceinline__ void twiddle(cf* v, const cf* tw, int t) {
+// Twiddle bases of one thread, loaded once per kernel and reused by every transform the
+// thread runs (they depend only on t): for the middle stage (radix R1, NS = 16) and the
+// last stage (radix 16, NS = L/16) the table entries W^e, W^4e, W^8e of each butterfly.
+template <int L, int R1>
+struct TwBase {
+    static constexpr int B1 = 16 / R1;
+    cf m1[B1], m4[B1], m8[B1];
+    cf l1, l4, l8;
+};
+
+template <int L, int R1, int TS>
+__device__ __forceinline__ TwBase<L, R1> load_tw_base(const cf* tw, int t) {
     constexpr int T = L / 16;
-    constexpr int B = 16 / R;
-    constexpr int STEP = L / (NS * R);
+    constexpr int STEP1 = L / (16 * R1);
+    TwBase<L, R1> b;
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-        const int e = ((t + T * b) % NS) * STEP;  // exponent unit of this butterfly
-        cf w1 = ld_tw(tw, e * TS);
-        cf w4 = R > 4 ? ld_tw(tw, ((4 * e) % L) * TS) : w1;
-        cf w8 = R > 8 ? ld_tw(tw, ((8 * e) % L) * TS) : w1;
-        apply_powers<R>(v + b * R, w1, w4, w8);
+    for (int q = 0; q < TwBase<L, R1>::B1; ++q) {
+        const int e = ((t + T * q) % 16) * STEP1;
+        b.m1[q] = ld_tw(tw, e * TS);
+        b.m4[q] = R1 > 4 ? ld_tw(tw, ((4 * e) % L) * TS) : b.m1[q];
+        b.m8[q] = R1 > 8 ? ld_tw(tw, ((8 * e) % L) * TS) : b.m1[q];
     }
+    b.l1 = ld_tw(tw, t * TS);
+    b.l4 = ld_tw(tw, ((4 * t) % L) * TS);
+    b.l8 = ld_tw(tw, ((8 * t) % L) * TS);
+    return b;
 }
 
 // W_2L^(t + r T) for r < 16, from the table entry W_2L^t (tw has W_2L^m at tw[m]) and the
 // constants W_2L^(r T) = W_32^r (T = L / 16)
 __device__ __forceinline__ cf twist(cf wt, int r) { return cmul(wt, w32(r)); }
 
+// W_2L^-(t + r T) from the table entry W_2L^(2L - t) (= W_2L^-t) and conj(W_32^r).  Written
+// from a different table entry than twist() on purpose: the compiler cannot merge the two,
+// so the factors are not kept alive across the transforms in between.
+__device__ __forceinline__ cf untwist(cf wtc, int r) { return cmulc(wtc, w32(r)); }
+
 // Forward FFT of length L = 16 * R1 * 16; v natural strided in and out.  buf: this line's
-// shared buffer (L + L/16 values).  tw: table with W_L^m at tw[m * TS].
-template <int L, int R1, int TS>
-__device__ __forceinline__ void fft(cf* v, cf* buf, const cf* tw, int t) {
+// shared buffer (L + L/16 values).  tb: the thread's twiddle bases (load_tw_base).
+template <int L, int R1>
+__device__ __forceinline__ void fft(cf* v, cf* buf, const TwBase<L, R1>& tb, int t) {
     static_assert(16 * R1 * 16 == L, "L = 16 * R1 * 16");
     butterflies<16>(v);
     exchange<L, 16, 1, R1>(v, buf, t);
-    twiddle<L, R1, 16, TS>(v, tw, t);
+#pragma unroll
+    for (int q = 0; q < TwBase<L, R1>::B1; ++q) apply_powers<R1>(v + q * R1, tb.m1[q], tb.m4[q], tb.m8[q]);
     butterflies<R1>(v);
     exchange<L, R1, 16, 16>(v, buf, t);
-    twiddle<L, 16, 16 * R1, TS>(v, tw, t);
+    apply_powers<16>(v, tb.l1, tb.l4, tb.l8);
     butterflies<16>(v);
 }
 
-template <int L, int R1, int TS>
-__device__ __forceinline__ void ifft(cf* v, cf* buf, const cf* tw, int t) {
+template <int L, int R1>
+__device__ __forceinline__ void ifft(cf* v, cf* buf, const TwBase<L, R1>& tb, int t) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
-    fft<L, R1, TS>(v, buf, tw, t);
+    fft<L, R1>(v, buf, tb, t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
 }
