@@ -202,14 +202,16 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
         // row into shared memory with one pad word per 16 (the solve's per-thread chunks
         // of 16 then fall in distinct banks)
         const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * L);
-        for (int q = t; q < L / 4; q += T) {
-            float4 x = src[q];
-            int e = 4 * q;
-            float* d = rbuf + pad(e);
-            d[0] = x.x;
-            d[1] = x.y;
-            d[2] = x.z;
-            d[3] = x.w;
+        float4 x[4];  // all loads in flight before the first shared store
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = src[t + q * T];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float* d = rbuf + pad(4 * (t + q * T));
+            d[0] = x[q].x;
+            d[1] = x[q].y;
+            d[2] = x[q].z;
+            d[3] = x[q].w;
         }
         fill_lambda(lam);
         __syncthreads();
@@ -309,7 +311,13 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
                      : "memory");
     }
     const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
-    for (int i = t; i < L; i += T) xb[pad(i)] = zc[(size_t)i * kTW];
+    {
+        cf x[16];  // all loads in flight before the first shared store
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = ld2(zc + (size_t)(t + r * T) * kTW);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = x[r];
+    }
     if (solve) fill_lambda(lam);
     __syncthreads();
     if (solve) solve_line_fast<cf, 16>(xb, eb, xb, L, t, lam);
@@ -392,7 +400,13 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols_split(con
     const size_t slab = (size_t)L * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
     const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
-    for (int i = t; i < L; i += T) xb[pad(i)] = zc[(size_t)i * kTW];
+    {
+        cf x[16];  // all loads in flight before the first shared store
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = ld2(zc + (size_t)(t + r * T) * kTW);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = x[r];
+    }
     if (solve) fill_lambda(lam);
     __syncthreads();
     if (solve) solve_line_fast<cf, 16>(xb, eb, xb, L, t, lam);
@@ -440,10 +454,19 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restric
     const size_t slab = (size_t)nx * kTW;
     const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
     // X[k], k = 0..L (the tile pair (2p, 2p + 1) of row i is one 16-byte word)
-    for (int p = t; p <= L / 2; p += T) {
-        float4 d = *reinterpret_cast<const float4*>(g + (size_t)p * slab + (size_t)i * kTW);
-        xb[pad(2 * p)] = mk(d.x, d.y);
-        xb[pad(2 * p + 1)] = mk(d.z, d.w);
+    {
+        float4 d[8];  // all loads in flight before the first shared store
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d[q] = *reinterpret_cast<const float4*>(g + (size_t)(t + q * T) * slab + (size_t)i * kTW);
+        float4 dl = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t == 0) dl = *reinterpret_cast<const float4*>(g + (size_t)(L / 2) * slab + (size_t)i * kTW);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int p = t + q * T;
+            xb[pad(2 * p)] = mk(d[q].x, d[q].y);
+            xb[pad(2 * p + 1)] = mk(d[q].z, d[q].w);
+        }
+        if (t == 0) xb[pad(L)] = mk(dl.x, dl.y);
     }
     __syncthreads();
     cf v[16];
