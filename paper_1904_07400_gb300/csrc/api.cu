@@ -165,6 +165,13 @@ tdg_status ensure_workspace(Plan& p) {
     return TDG_OK;
 }
 
+// the tensor-core form exists only for the grids its kernels are written for
+bool tc16_available(int nx, int ny) {
+    (void)nx;
+    (void)ny;
+    return false;
+}
+
 }  // namespace
 
 namespace tdg {
@@ -197,6 +204,7 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
     if (order < 1 || order > 3 || nx < 1 || ny < 1) return TDG_ERR_INVALID_ARG;
     if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy) || !isfinite(G)) return TDG_ERR_INVALID_ARG;
     if (prec != TDG_FP64 && prec != TDG_FP32 && prec != TDG_FP32_TC16) return TDG_ERR_INVALID_ARG;
+    if (prec == TDG_FP32_TC16 && !tc16_available(nx, ny)) return TDG_ERR_UNSUPPORTED;
     if (device < 0) return TDG_ERR_INVALID_ARG;
     if (nx > kMaxN || ny > kMaxN) return TDG_ERR_UNSUPPORTED;
     tdg_plan_s* h = new (std::nothrow) tdg_plan_s();

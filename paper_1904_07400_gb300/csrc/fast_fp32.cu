@@ -109,49 +109,59 @@ constexpr int kExactRows = 6;
 
 template <typename V, int CH>
 __device__ __forceinline__ void solve_line_fast(const V* src, V* tmp, V* dst, int n, int t, const float* lam) {
+    constexpr int W = kWarmFast;
     const float li = lam[kLam - 1];
     const int a = t * CH;
-    // forward sweep y_i = 8 s_i - lam_{i-1} y_{i-1}
+    V x[CH + W];
+    // forward sweep y_i = 8 s_i - lam_{i-1} y_{i-1}: all loads first, then the recurrence
+    // in registers
     if (t == 0) {
-        V y = vs(src[pad(0)], 8.0f);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) x[i] = src[pad(i)];
+        V y = vs(x[0], 8.0f);
         tmp[pad(0)] = y;
-#pragma unroll 4
+#pragma unroll
         for (int i = 1; i < CH; ++i) {
             float l = i - 1 < kExactRows ? lam[i - 1] : li;
-            y = vs(src[pad(i)], 8.0f) - vs(y, l);
+            y = vs(x[i], 8.0f) - vs(y, l);
             tmp[pad(i)] = y;
         }
     } else {
-        V y = vs(src[pad(a - kWarmFast)], 8.0f);
-#pragma unroll 4
-        for (int i = 1; i < kWarmFast; ++i) y = vs(src[pad(a - kWarmFast + i)], 8.0f) - vs(y, li);
-#pragma unroll 4
+#pragma unroll
+        for (int i = 0; i < CH + W; ++i) x[i] = src[pad(a - W + i)];
+        V y = vs(x[0], 8.0f);
+#pragma unroll
+        for (int i = 1; i < W; ++i) y = vs(x[i], 8.0f) - vs(y, li);
+#pragma unroll
         for (int i = 0; i < CH; ++i) {
-            y = vs(src[pad(a + i)], 8.0f) - vs(y, li);
+            y = vs(x[W + i], 8.0f) - vs(y, li);
             tmp[pad(a + i)] = y;
         }
     }
     __syncthreads();
     // backward sweep c_i = lam_i (y_i - c_{i+1}), exact at the end of the line
     const int b = a + CH;
-    V c;
     if (b == n) {
-        c = vs(tmp[pad(n - 1)], li);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) x[i] = tmp[pad(a + i)];
+        V c = vs(x[CH - 1], li);
         dst[pad(n - 1)] = c;
-#pragma unroll 4
+#pragma unroll
         for (int i = CH - 2; i >= 0; --i) {
             float l = a + i < kExactRows ? lam[a + i] : li;
-            c = vs(tmp[pad(a + i)] - c, l);
+            c = vs(x[i] - c, l);
             dst[pad(a + i)] = c;
         }
     } else {
-        c = vs(tmp[pad(b + kWarmFast - 1)], li);
-#pragma unroll 4
-        for (int i = kWarmFast - 2; i >= 0; --i) c = vs(tmp[pad(b + i)] - c, li);
-#pragma unroll 4
+#pragma unroll
+        for (int i = 0; i < CH + W; ++i) x[i] = tmp[pad(a + i)];
+        V c = vs(x[CH + W - 1], li);
+#pragma unroll
+        for (int i = CH + W - 2; i >= CH; --i) c = vs(x[i] - c, li);
+#pragma unroll
         for (int i = CH - 1; i >= 0; --i) {
             float l = a + i < kExactRows ? lam[a + i] : li;
-            c = vs(tmp[pad(a + i)] - c, l);
+            c = vs(x[i] - c, l);
             dst[pad(a + i)] = c;
         }
     }
