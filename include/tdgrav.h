@@ -55,6 +55,7 @@ typedef enum {
 } tdg_precision;
 
 typedef struct tdg_plan_s* tdg_plan;
+typedef struct tdg_batch_s* tdg_batch;
 typedef struct CUstream_st* tdg_stream;
 
 /* Create a plan for an nx x ny grid of cells dx x dy, B-spline order 1..3, constant G.
@@ -85,15 +86,52 @@ tdg_status tdg_set_workspace(tdg_plan p, void* ptr, size_t bytes);
 tdg_status tdg_solve_forces(tdg_plan p, const void* sigma, void* fx, void* fy,
                             tdg_stream stream);
 
-/* `count` independent solves, each with its own plan (any nx, ny, order; all plans must
- * share one precision and device), executed by one persistent launch that walks a work
- * list of (grid, pass, tile) items in pass order.  sigma[d], fx[d], fy[d] follow the
- * layout of tdg_solve_forces for plans[d].  Errors: as tdg_solve_forces, INVALID_ARG for
- * mixed precisions/devices; a device-side dependency wait that exceeds its bound sets the
- * error word read by tdg_get_device_error (TIMEOUT) instead of hanging. */
+/* `count` independent solves, each with its own plan (any nx, ny, order; FP32 plans on
+ * one device), executed by one persistent launch (see tdg_batch_create).  Convenience form:
+ * creates a batch, launches it on `stream` and releases it, which synchronises the device
+ * before returning.  For repeated solves create the batch once and launch it (that launch
+ * is asynchronous).  sigma[d], fx[d], fy[d] follow the layout of tdg_solve_forces for
+ * plans[d].  Errors: as tdg_batch_create and tdg_batch_launch. */
 tdg_status tdg_solve_forces_batched(const tdg_plan* plans, int count,
                                     const void* const* sigma, void* const* fx,
                                     void* const* fy, tdg_stream stream);
+
+/* A reusable batch of independent solves (meshes or disks of uneven sizes and orders,
+ * paper Sec. 1 motivates such uses): per-grid descriptors, one workspace and dependency
+ * counters on the device.  The pointers are captured at creation; the plans must outlive
+ * the batch and keep their kernel tables.  Errors: INVALID_ARG (NULL or misaligned
+ * pointers, mixed devices), NOT_BUILT, UNSUPPORTED (FP64 or TC16 plans, a grid whose
+ * passes do not fit one block), OOM, CUDA. */
+tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count,
+                            const void* const* sigma, void* const* fx, void* const* fy);
+
+/* Tuning knobs of the persistent kernel (picked by the autotuner): threads per block
+ * (256 or 512) and radix preference of the transforms (0: radix 8 first, 1: radix
+ * 4).  Errors: INVALID_ARG, UNSUPPORTED (a grid does not fit; the old setting stays). */
+tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref);
+
+/* One persistent launch solving every grid of the batch on `stream`: a memset of the
+ * dependency counters and one kernel, no host synchronisation.  Work items (row groups,
+ * frequency columns, inverse-row groups) are taken in pass order; an item waits for its
+ * own grid's previous pass with a bounded spin (about one second), after which it sets
+ * the batch error word to TDG_ERR_TIMEOUT and is skipped.  Errors: INVALID_ARG, CUDA. */
+tdg_status tdg_batch_launch(tdg_batch b, tdg_stream stream);
+
+/* Read and clear the batch's device error word (synchronises).  TDG_OK or TIMEOUT. */
+tdg_status tdg_batch_get_error(tdg_batch b);
+
+/* Blocks of the persistent launch, threads per block, total work items and radix
+ * preference.  Any out pointer may be NULL. */
+tdg_status tdg_batch_info(const tdg_batch b, int* blocks, int* threads, int* items,
+                          int* radix_pref);
+
+/* Test hook: completions of grid `grid`'s row pass are not counted by later launches
+ * (-1 restores normal operation), so its column items exhaust their bounded wait.
+ * Exists to test the timeout path without faulting or hanging the device. */
+tdg_status tdg_batch_debug_withhold(tdg_batch b, int grid);
+
+/* Release the batch (synchronises its device). */
+tdg_status tdg_batch_destroy(tdg_batch b);
 
 /* Adjoint of tdg_solve_forces: for L = sum(gfx * F^x + gfy * F^y), write
  * gsigma = dL/dsigma = (B-spline solve)^T (correlation of gfx, gfy with the same kernel

@@ -128,6 +128,61 @@ class Plan:
             pass
 
 
+class Batch:
+    """Many independent FP32 solves in one persistent launch (tdg_batch_*).
+
+    The grids' input and output tensors are bound at creation; ``launch()`` solves all of
+    them on the current stream with one kernel and no host synchronisation, so it can be
+    captured in a CUDA graph.
+    """
+
+    def __init__(self, plans: list[Plan], sigmas: list[torch.Tensor], outs: list[tuple] | None = None):
+        if outs is None:
+            outs = [(torch.empty_like(s), torch.empty_like(s)) for s in sigmas]
+        for p, s, (fx, fy) in zip(plans, sigmas, outs):
+            p._check(s, "sigma")
+            p._check(fx, "fx")
+            p._check(fy, "fy")
+        self.plans, self.sigmas, self.outs = list(plans), list(sigmas), list(outs)
+        n = len(plans)
+        arr = ctypes.c_void_p * n
+        h = ctypes.c_void_p()
+        native.call("tdg_batch_create", ctypes.byref(h), arr(*[p.handle.value for p in plans]), n,
+                    arr(*[_ptr(s) for s in sigmas]), arr(*[_ptr(o[0]) for o in outs]),
+                    arr(*[_ptr(o[1]) for o in outs]))
+        self._h = h
+        self.device = plans[0].device
+
+    def set_config(self, threads: int, radix_pref: int) -> None:
+        native.call("tdg_batch_set_config", self._h, threads, radix_pref)
+
+    def info(self) -> dict:
+        b, t, i, r = (ctypes.c_int() for _ in range(4))
+        native.call("tdg_batch_info", self._h, ctypes.byref(b), ctypes.byref(t), ctypes.byref(i), ctypes.byref(r))
+        return {"blocks": b.value, "threads": t.value, "items": i.value, "radix_pref": r.value}
+
+    def launch(self) -> None:
+        native.call("tdg_batch_launch", self._h, _stream_handle(self.device))
+
+    def error(self) -> int:
+        return int(native.load().tdg_batch_get_error(self._h))
+
+    def withhold(self, grid: int) -> None:
+        """Test hook: do not count grid `grid`'s row-pass completions (-1 to undo)."""
+        native.call("tdg_batch_debug_withhold", self._h, grid)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            native.load().tdg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def forces_batched(plans: list[Plan], sigmas: list[torch.Tensor], outs: list[tuple] | None = None):
     """Solve many independent grids in one library call."""
     n = len(plans)

@@ -380,19 +380,13 @@ tdg_status tdg_solve_adjoint(tdg_plan h, const void* gfx, const void* gfy, void*
 
 tdg_status tdg_solve_forces_batched(const tdg_plan* plans, int count, const void* const* sigma, void* const* fx,
                                     void* const* fy, tdg_stream stream) {
-    if (!plans || count < 0 || (count > 0 && (!sigma || !fx || !fy))) return TDG_ERR_INVALID_ARG;
-    for (int d = 0; d < count; ++d) {
-        if (!plans[d]) return TDG_ERR_INVALID_ARG;
-        if (plans[d]->p.prec != plans[0]->p.prec || plans[d]->p.device != plans[0]->p.device)
-            return TDG_ERR_INVALID_ARG;
-        tdg_status st = check_solve_args(plans[d]->p, sigma[d], fx[d], fy[d]);
-        if (st != TDG_OK) return st;
-    }
-    for (int d = 0; d < count; ++d) {
-        tdg_status st = tdg_solve_forces(plans[d], sigma[d], fx[d], fy[d], stream);
-        if (st != TDG_OK) return st;
-    }
-    return TDG_OK;
+    if (count == 0 && plans) return TDG_OK;
+    tdg_batch b = nullptr;
+    tdg_status st = tdg_batch_create(&b, plans, count, sigma, fx, fy);
+    if (st != TDG_OK) return st;
+    st = tdg_batch_launch(b, stream);
+    tdg_status st2 = tdg_batch_destroy(b);
+    return st != TDG_OK ? st : st2;
 }
 
 tdg_status tdg_get_device_error(tdg_plan h) {

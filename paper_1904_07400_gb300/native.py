@@ -30,6 +30,15 @@ SIGNATURES = [
     ("tdg_solve_forces", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_solve_forces_batched", _c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p),
                                           ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), _c_void_p]),
+    ("tdg_batch_create", _c_int, [ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), _c_int,
+                                  ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p)]),
+    ("tdg_batch_set_config", _c_int, [_c_void_p, _c_int, _c_int]),
+    ("tdg_batch_launch", _c_int, [_c_void_p, _c_void_p]),
+    ("tdg_batch_get_error", _c_int, [_c_void_p]),
+    ("tdg_batch_info", _c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                ctypes.POINTER(_c_int)]),
+    ("tdg_batch_debug_withhold", _c_int, [_c_void_p, _c_int]),
+    ("tdg_batch_destroy", _c_int, [_c_void_p]),
     ("tdg_solve_adjoint", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_get_device_error", _c_int, [_c_void_p]),
     ("tdg_copy_kernel_tables", _c_int, [_c_void_p, _c_void_p, _c_void_p]),

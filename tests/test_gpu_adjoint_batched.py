@@ -115,8 +115,11 @@ def test_batched_equals_individual_solves():
         refs.append(p.forces(s))
     outs = forces_batched(plans, sigmas)
     torch.cuda.synchronize()
+    # the batched kernel runs the transforms with another thread layout: equal to rounding
     for (ax, ay), (bx, by) in zip(outs, refs):
-        assert torch.equal(ax, bx) and torch.equal(ay, by)
+        num = float(((ax - bx) ** 2).sum() + ((ay - by) ** 2).sum()) ** 0.5
+        den = float((bx ** 2).sum() + (by ** 2).sum()) ** 0.5
+        assert num <= TOL_FP32 * den
 
 
 def test_error_paths():
