@@ -194,8 +194,8 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // L, period 2L).  Several blocks share an SM, so one block's barrier waits overlap with
 // another's work.
 // ---------------------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict__ sigma, int nx, int solve,
+template <int L, bool TC>
+__global__ void __launch_bounds__(L / 16, TC ? 2 : 3) k_fast_rows(const float* __restrict__ sigma, int nx, int solve,
                                                          const cf* __restrict__ tw, cf* __restrict__ z) {
     constexpr int T = L / 16;
     constexpr int R1 = reg::Mid<L>::R1;
@@ -207,6 +207,9 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
     const int t = threadIdx.x;
     const int i = blockIdx.x;
     const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
+    cf* ws = TC ? reinterpret_cast<cf*>(lam + kLam) + (t >> 5) * reg::kTcWarpScratch : nullptr;
+    reg::TcConst K;
+    if constexpr (TC) K = reg::make_tc_const(t & 31);
     cf v[16];
     if (solve) {
         // row into shared memory with one pad word per 16 (the solve's per-thread chunks
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows(const float* __restrict
     }
 #pragma unroll
     for (int r = 8; r < 16; ++r) v[r] = mk(0.f, 0.f);
-    reg::fft<L, R1>(v, eb, tb, t);
+    reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
     // unpack the real transform: X[k] from Z[k] and Z[L - k]
 #pragma unroll
     for (int r = 0; r < 16; ++r) eb[pad(t + r * T)] = v[r];
@@ -291,8 +294,8 @@ __device__ __forceinline__ void spec_products(cf* wx, cf* v, const float2* sh, i
 #define TDG_COLS_SPLIT 0
 #endif
 
-template <int L>
-__global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf* __restrict__ z, int hy, int solve,
+template <int L, bool TC>
+__global__ void __launch_bounds__(L / 16, TC ? 1 : TDG_COLS_BLOCKS) k_fast_cols(const cf* __restrict__ z, int hy, int solve,
                                                          const cf* __restrict__ tw,
                                                          const float2* __restrict__ spec, cf* __restrict__ gx,
                                                          cf* __restrict__ gy) {
@@ -306,6 +309,9 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
     cf* sb = eb + LP;                            // LP: the even-half x result
     float* lam = reinterpret_cast<float*>(sb + LP);
     const int t = threadIdx.x;
+    cf* ws = TC ? reinterpret_cast<cf*>(lam + kLam) + (t >> 5) * reg::kTcWarpScratch : nullptr;
+    reg::TcConst K;
+    if constexpr (TC) K = reg::make_tc_const(t & 31);
     const int ky = blockIdx.x;
     const int tile = ky >> 1, c = ky & 1;
     const size_t slab = (size_t)L * kTW;
@@ -339,12 +345,12 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
     // even frequencies: X_e = FFT_N(x); both products; both inverse transforms
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
-    reg::fft<L, R1>(v, eb, tb, t);
+    reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
     spec_products<L, 0>(w, v, se, t);
-    reg::ifft<L, R1>(w, eb, tb, t);
+    reg::ifft<L, R1, TC>(w, eb, tb, t, ws, &K);
 #pragma unroll
     for (int r = 0; r < 16; ++r) sb[pad(t + r * T)] = w[r];  // own positions only
-    reg::ifft<L, R1>(v, eb, tb, t);
+    reg::ifft<L, R1, TC>(v, eb, tb, t, ws, &K);
     // odd frequencies: read the twisted column, then park the even y result in its place
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -352,11 +358,11 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
         w[r] = cmul(xb[pad(n)], reg::twist(wt, r));  // x_n W_2L^n
         xb[pad(n)] = v[r];
     }
-    reg::fft<L, R1>(w, eb, tb, t);
+    reg::fft<L, R1, TC>(w, eb, tb, t, ws, &K);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = w[r];
     spec_products<L, 1>(w, v, so, t);
-    reg::ifft<L, R1>(w, eb, tb, t);
+    reg::ifft<L, R1, TC>(w, eb, tb, t, ws, &K);
     cf* gxc = gx + (size_t)tile * slab + c;
     cf* gyc = gy + (size_t)tile * slab + c;
     const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols(const cf*
         int n = t + r * T;
         gxc[(size_t)n * kTW] = sb[pad(n)] + cmul(w[r], reg::untwist(wtc, r));
     }
-    reg::ifft<L, R1>(v, eb, tb, t);
+    reg::ifft<L, R1, TC>(v, eb, tb, t, ws, &K);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         int n = t + r * T;
@@ -390,7 +396,7 @@ __device__ __forceinline__ void spec_product_one(cf* v, const float2* sh, int co
     }
 }
 
-template <int L>
+template <int L, bool TC = false>
 __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols_split(const cf* __restrict__ z, int hy, int solve,
                                                                const cf* __restrict__ tw,
                                                                const float2* __restrict__ spec,
@@ -410,6 +416,8 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols_split(con
     const size_t slab = (size_t)L * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
     const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
+    cf* ws = nullptr;  // no tensor-core stages in this variant
+    reg::TcConst K;
     {
         cf x[16];  // all loads in flight before the first shared store
 #pragma unroll
@@ -425,16 +433,16 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols_split(con
     cf v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
-    reg::fft<L, R1>(v, eb, tb, t);
+    reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
     spec_product_one<L, 0>(v, se, comp, t);
-    reg::ifft<L, R1>(v, eb, tb, t);
+    reg::ifft<L, R1, TC>(v, eb, tb, t, ws, &K);
 #pragma unroll
     for (int r = 0; r < 16; ++r) sb[pad(t + r * T)] = v[r];
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(xb[pad(t + r * T)], reg::twist(wt, r));
-    reg::fft<L, R1>(v, eb, tb, t);
+    reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
     spec_product_one<L, 1>(v, se + HS, comp, t);
-    reg::ifft<L, R1>(v, eb, tb, t);
+    reg::ifft<L, R1, TC>(v, eb, tb, t, ws, &K);
     cf* gc = (comp ? gy : gx) + (size_t)tile * slab + c;
     const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
 #pragma unroll
@@ -447,8 +455,8 @@ __global__ void __launch_bounds__(L / 16, TDG_COLS_BLOCKS) k_fast_cols_split(con
 // ---------------------------------------------------------------------------------------
 // pass C: one row of one component per block (blockIdx.y = component)
 // ---------------------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restrict__ g0,
+template <int L, bool TC>
+__global__ void __launch_bounds__(L / 16, TC ? 2 : 3) k_fast_rows_inv(const cf* __restrict__ g0,
                                                              const cf* __restrict__ g1, int nx,
                                                              const cf* __restrict__ tw, float* __restrict__ f0,
                                                              float* __restrict__ f1) {
@@ -460,6 +468,9 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restric
     const cf* g = blockIdx.y ? g1 : g0;
     float* f = blockIdx.y ? f1 : f0;
     const int t = threadIdx.x;
+    cf* ws = TC ? xb + LP + (t >> 5) * reg::kTcWarpScratch : nullptr;
+    reg::TcConst K;
+    if constexpr (TC) K = reg::make_tc_const(t & 31);
     const int i = blockIdx.x;
     const size_t slab = (size_t)nx * kTW;
     const reg::TwBase<L, R1> tb = reg::load_tw_base<L, R1, 2>(tw, t);
@@ -487,7 +498,7 @@ __global__ void __launch_bounds__(L / 16, 3) k_fast_rows_inv(const cf* __restric
         v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::twist(wt, r));
     }
     __syncthreads();
-    reg::ifft<L, R1>(v, xb, tb, t);
+    reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K);
     float2* out = reinterpret_cast<float2*>(f + (size_t)i * L);
 #pragma unroll
     for (int r = 0; r < 8; ++r) out[t + r * T] = make_float2(v[r].x, v[r].y);
@@ -514,24 +525,31 @@ __global__ void k_half_spectra(const float* __restrict__ full, int hy, int Px, f
 }
 
 template <int L>
-size_t rows_smem(int solve) {
-    constexpr int LP = L + L / 16 + 16;
-    return LP * sizeof(cf) + (solve ? LP * sizeof(float) : 0) + kLam * sizeof(float);
+size_t tc_scratch(bool tc) {
+    return tc ? (size_t)(L / 16 / 32) * reg::kTcWarpScratch * sizeof(cf) : 0;
 }
 
 template <int L>
-size_t cols_smem() {
+size_t rows_smem(int solve, bool tc) {
     constexpr int LP = L + L / 16 + 16;
-    return 3 * LP * sizeof(cf) + kLam * sizeof(float);
+    // the order-3 row buffer is always reserved so the TC scratch has a fixed offset
+    return LP * sizeof(cf) + LP * sizeof(float) + kLam * sizeof(float) + tc_scratch<L>(tc);
+    (void)solve;
 }
 
 template <int L>
-size_t inv_smem() {
+size_t cols_smem(bool tc) {
     constexpr int LP = L + L / 16 + 16;
-    return LP * sizeof(cf);
+    return 3 * LP * sizeof(cf) + kLam * sizeof(float) + tc_scratch<L>(tc);
 }
 
-template <int LX, int LY>
+template <int L>
+size_t inv_smem(bool tc) {
+    constexpr int LP = L + L / 16 + 16;
+    return LP * sizeof(cf) + tc_scratch<L>(tc);
+}
+
+template <int LX, int LY, bool TC>
 cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     const int hy = p.hy;
     const int ntile = (hy + kTW - 1) / kTW;
@@ -543,43 +561,52 @@ cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, vo
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
     const int solve = p.order == 3;
     cudaError_t e;
-    size_t sm = rows_smem<LY>(solve);
-    if ((e = cudaFuncSetAttribute(k_fast_rows<LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    size_t sm = rows_smem<LY>(solve, TC);
+    if ((e = cudaFuncSetAttribute(k_fast_rows<LY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
         return e;
     mark(p, 0, s);
-    k_fast_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, p.nx, solve, twy, z);
+    k_fast_rows<LY, TC><<<p.nx, LY / 16, sm, s>>>(sigma, p.nx, solve, twy, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
-    sm = cols_smem<LX>();
+    sm = cols_smem<LX>(TC);
 #if TDG_COLS_SPLIT
     if ((e = cudaFuncSetAttribute(k_fast_cols_split<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
         return e;
     k_fast_cols_split<LX><<<2 * hy, LX / 16, sm, s>>>(z, hy, solve, twx,
                                                        reinterpret_cast<const float2*>(p.spec_half), gx, gy);
 #else
-    if ((e = cudaFuncSetAttribute(k_fast_cols<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    if ((e = cudaFuncSetAttribute(k_fast_cols<LX, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
         return e;
-    k_fast_cols<LX><<<hy, LX / 16, sm, s>>>(z, hy, solve, twx, reinterpret_cast<const float2*>(p.spec_half), gx,
-                                             gy);
+    k_fast_cols<LX, TC><<<hy, LX / 16, sm, s>>>(z, hy, solve, twx, reinterpret_cast<const float2*>(p.spec_half), gx,
+                                                 gy);
 #endif
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
-    sm = inv_smem<LY>();
-    if ((e = cudaFuncSetAttribute(k_fast_rows_inv<LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    sm = inv_smem<LY>(TC);
+    if ((e = cudaFuncSetAttribute(k_fast_rows_inv<LY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
         return e;
     dim3 grid(p.nx, 2);
-    k_fast_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gx, gy, p.nx, twy, fx, fy);
+    k_fast_rows_inv<LY, TC><<<grid, LY / 16, sm, s>>>(gx, gy, p.nx, twy, fx, fy);
     e = cudaGetLastError();
     mark(p, 3, s);
     return e;
 }
 
-template <int LX>
+template <int LX, bool TC>
 cudaError_t run_fast_x(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     switch (p.ny) {
-        case 1024: return run_fast<LX, 1024>(p, sigma, fx, fy, work, s);
-        case 2048: return run_fast<LX, 2048>(p, sigma, fx, fy, work, s);
-        default: return run_fast<LX, 4096>(p, sigma, fx, fy, work, s);
+        case 1024: return run_fast<LX, 1024, TC>(p, sigma, fx, fy, work, s);
+        case 2048: return run_fast<LX, 2048, TC>(p, sigma, fx, fy, work, s);
+        default: return run_fast<LX, 4096, TC>(p, sigma, fx, fy, work, s);
+    }
+}
+
+template <bool TC>
+cudaError_t run_fast_xy(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+    switch (p.nx) {
+        case 1024: return run_fast_x<1024, TC>(p, sigma, fx, fy, work, s);
+        case 2048: return run_fast_x<2048, TC>(p, sigma, fx, fy, work, s);
+        default: return run_fast_x<4096, TC>(p, sigma, fx, fy, work, s);
     }
 }
 
@@ -606,11 +633,8 @@ cudaError_t launch_half_spectra(const Plan& p, cudaStream_t s) {
 
 cudaError_t launch_forward_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                 cudaStream_t s) {
-    switch (p.nx) {
-        case 1024: return run_fast_x<1024>(p, sigma, fx, fy, work, s);
-        case 2048: return run_fast_x<2048>(p, sigma, fx, fy, work, s);
-        default: return run_fast_x<4096>(p, sigma, fx, fy, work, s);
-    }
+    if (p.prec == TDG_FP32_TC16) return run_fast_xy<true>(p, sigma, fx, fy, work, s);
+    return run_fast_xy<false>(p, sigma, fx, fy, work, s);
 }
 
 }  // namespace tdg

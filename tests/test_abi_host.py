@@ -71,6 +71,12 @@ def test_init_validates_arguments(lib):
         assert st == 1 and not h.value, args
     st, _ = _init(lib, 4097, 64, 3, 0.1, 0.1, 1.0, 1, 0)
     assert st == 2
+    # the tensor-core form exists for sides of 1024, 2048 and 4096 cells only
+    st, h = _init(lib, 512, 512, 3, 0.1, 0.1, 1.0, 2, 0)
+    assert st == 2 and not h.value
+    st, h = _init(lib, 4096, 1024, 3, 0.1, 0.1, 1.0, 2, 0)
+    assert st == 0
+    lib.tdg_destroy(h)
     assert lib.tdg_init(None, 64, 64, 3, 0.1, 0.1, 1.0, 1, 0) == 1
 
 

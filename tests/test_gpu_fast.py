@@ -62,3 +62,23 @@ def test_fast_path_edges_and_ragged_support():
     rx, ry = oracle_solver(nx, ny, 3, dx, dx).forces(sigma)
     f32 = _forces(nx, ny, 3, dx, dx, "fp32", sigma)
     assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
+
+
+@pytest.mark.parametrize("shape,k", [((1024, 1024), 3), ((2048, 1024), 2), ((1024, 4096), 1), ((4096, 4096), 3)])
+def test_tc16_form_vs_fp64_gpu(shape, k):
+    # radix-16 stages as split FP16 hi/lo tensor-core products, FP32 accumulation
+    nx, ny = shape
+    dx, dy = 1.0 / nx, 1.0 / ny
+    sigma = syn.clumps(nx, ny, seed=3 + k)
+    tc = _forces(nx, ny, k, dx, dy, "fp32_tc16", sigma)
+    f64 = _forces(nx, ny, k, dx, dy, "fp64", sigma)
+    assert rel_l2_pair(*tc, *f64) <= TOL_FP32
+
+
+def test_tc16_form_vs_oracle():
+    nx, ny = 1024, 2048
+    dx, dy = 1.0 / 1024, 0.5 / 2048
+    sigma = syn.clumps(nx, ny, seed=12)
+    rx, ry = oracle_solver(nx, ny, 3, dx, dy).forces(sigma)
+    tc = _forces(nx, ny, 3, dx, dy, "fp32_tc16", sigma)
+    assert rel_l2_pair(*tc, rx, ry) <= TOL_FP32
