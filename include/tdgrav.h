@@ -189,8 +189,11 @@ tdg_status tdg_solve_forces_noalloc(tdg_plan p, const void* sigma, void* fx, voi
 tdg_status tdg_plan_info(const tdg_plan p, int* px, int* py, int* order, int* precision);
 
 /* Kernel path a forward solve of this plan runs: 0 = generic (any size, FP64 and FP32;
- * full spectra), 1 = FP32 register-transform path (sides of 1024, 2048 or 4096 cells;
- * half spectra).  Valid after tdg_build_kernel_tables; -1 for a NULL plan. */
+ * full spectra), 1 = register-transform path with two exchanges per transform (the
+ * FP32_TC16 form; sides of 1024, 2048 or 4096 cells; half spectra), 2 = FP32 one-barrier
+ * transform network with TMA tile movement (sides of 1024, 2048 or 4096 cells; half
+ * spectra in the network's order).  Valid after tdg_build_kernel_tables; -1 for a NULL
+ * plan. */
 int tdg_plan_path(const tdg_plan p);
 
 /* Release everything the plan owns (synchronises its device first). */

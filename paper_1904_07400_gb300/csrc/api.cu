@@ -137,10 +137,11 @@ void free_plan_memory(Plan& p) {
     cudaFree(p.tw_y);
     cudaFree(p.spec);
     cudaFree(p.spec_half);
+    cudaFree(p.net_tw);
     cudaFree(p.wq);
     cudaFree(p.err);
     if (p.work_owned) cudaFree(p.work);
-    p.tw_x = p.tw_y = p.spec = p.spec_half = nullptr;
+    p.tw_x = p.tw_y = p.spec = p.spec_half = p.net_tw = nullptr;
     p.wq = nullptr;
     p.err = nullptr;
     p.work = nullptr;
@@ -305,7 +306,13 @@ tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
         TDG_TRY(launch_spectra<float>(p, placed_x, placed_y, scratch, reinterpret_cast<float*>(p.spec), s));
     if (fast_fp32_eligible(p)) {
         TDG_TRY(cudaMalloc(&p.spec_half, fast_fp32_spec_bytes(p)));
-        TDG_TRY(launch_half_spectra(p, s));
+        if (net_fp32_eligible(p)) {
+            // FP32: one-barrier network kernels, spectra in the network's order
+            TDG_TRY(cudaMalloc(&p.net_tw, net_fp32_table_bytes(p)));
+            TDG_TRY(launch_net_tables(p, s));
+        } else {
+            TDG_TRY(launch_half_spectra(p, s));
+        }
     }
     TDG_TRY(cudaStreamSynchronize(s));
     cudaFree(placed_x);
@@ -450,6 +457,7 @@ tdg_status tdg_plan_info(const tdg_plan h, int* px, int* py, int* order, int* pr
 
 int tdg_plan_path(const tdg_plan h) {
     if (!h) return -1;
+    if (h->p.spec_half && h->p.net_tw) return 2;
     return (h->p.spec_half && fast_fp32_eligible(h->p)) ? 1 : 0;
 }
 

@@ -27,6 +27,11 @@ using reg::pad;
 
 constexpr int kTW = 2;  // tile width of the intermediates
 
+// 1: the row kernels give each transform's two exchanges separate shared buffers
+#ifndef TDG_DB
+#define TDG_DB 0
+#endif
+
 // ---------------------------------------------------------------------------------------
 // truncated tridiagonal solve (1/8)(c_{i-1} + 6 c_i + c_{i+1}) = s_i on one line held in
 // shared memory (element i at idx(i)); tpl threads per line, thread t owns a contiguous
@@ -244,7 +249,13 @@ __global__ void __launch_bounds__(L / 16, TC ? 2 : 3) k_fast_rows(const float* _
     }
 #pragma unroll
     for (int r = 8; r < 16; ++r) v[r] = mk(0.f, 0.f);
-    reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
+    if constexpr (TDG_DB && !TC) {
+        // the second exchange buffer overlays the row buffer and lam: every thread has
+        // read them before the first exchange's barrier
+        reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K, reinterpret_cast<cf*>(rbuf));
+    } else {
+        reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
+    }
     // unpack the real transform: X[k] from Z[k] and Z[L - k]
 #pragma unroll
     for (int r = 0; r < 16; ++r) eb[pad(t + r * T)] = v[r];
@@ -498,7 +509,8 @@ __global__ void __launch_bounds__(L / 16, TC ? 2 : 3) k_fast_rows_inv(const cf* 
         v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::twist(wt, r));
     }
     __syncthreads();
-    reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K);
+    if constexpr (TDG_DB && !TC) reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K, xb + LP);
+    else reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K);
     float2* out = reinterpret_cast<float2*>(f + (size_t)i * L);
 #pragma unroll
     for (int r = 0; r < 8; ++r) out[t + r * T] = make_float2(v[r].x, v[r].y);
@@ -533,8 +545,9 @@ template <int L>
 size_t rows_smem(int solve, bool tc) {
     constexpr int LP = L + L / 16 + 16;
     // the order-3 row buffer is always reserved so the TC scratch has a fixed offset
-    return LP * sizeof(cf) + LP * sizeof(float) + kLam * sizeof(float) + tc_scratch<L>(tc);
     (void)solve;
+    if (TDG_DB && !tc) return 2 * LP * sizeof(cf);
+    return LP * sizeof(cf) + LP * sizeof(float) + kLam * sizeof(float) + tc_scratch<L>(tc);
 }
 
 template <int L>
@@ -546,7 +559,21 @@ size_t cols_smem(bool tc) {
 template <int L>
 size_t inv_smem(bool tc) {
     constexpr int LP = L + L / 16 + 16;
+    if (TDG_DB && !tc) return 2 * LP * sizeof(cf);
     return LP * sizeof(cf) + tc_scratch<L>(tc);
+}
+
+#ifndef TDG_CARVE
+#define TDG_CARVE 0
+#endif
+
+// dynamic shared memory of a kernel; with TDG_CARVE the whole unified L1 / shared array
+// is requested as shared memory, so the occupancy the shared size allows is reached
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e || !TDG_CARVE) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 template <int LX, int LY, bool TC>
@@ -562,7 +589,7 @@ cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, vo
     const int solve = p.order == 3;
     cudaError_t e;
     size_t sm = rows_smem<LY>(solve, TC);
-    if ((e = cudaFuncSetAttribute(k_fast_rows<LY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    if ((e = set_smem(k_fast_rows<LY, TC>, sm)))
         return e;
     mark(p, 0, s);
     k_fast_rows<LY, TC><<<p.nx, LY / 16, sm, s>>>(sigma, p.nx, solve, twy, z);
@@ -570,12 +597,12 @@ cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, vo
     mark(p, 1, s);
     sm = cols_smem<LX>(TC);
 #if TDG_COLS_SPLIT
-    if ((e = cudaFuncSetAttribute(k_fast_cols_split<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    if ((e = set_smem(k_fast_cols_split<LX>, sm)))
         return e;
     k_fast_cols_split<LX><<<2 * hy, LX / 16, sm, s>>>(z, hy, solve, twx,
                                                        reinterpret_cast<const float2*>(p.spec_half), gx, gy);
 #else
-    if ((e = cudaFuncSetAttribute(k_fast_cols<LX, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    if ((e = set_smem(k_fast_cols<LX, TC>, sm)))
         return e;
     k_fast_cols<LX, TC><<<hy, LX / 16, sm, s>>>(z, hy, solve, twx, reinterpret_cast<const float2*>(p.spec_half), gx,
                                                  gy);
@@ -583,7 +610,7 @@ cudaError_t run_fast(const Plan& p, const float* sigma, float* fx, float* fy, vo
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
     sm = inv_smem<LY>(TC);
-    if ((e = cudaFuncSetAttribute(k_fast_rows_inv<LY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    if ((e = set_smem(k_fast_rows_inv<LY, TC>, sm)))
         return e;
     dim3 grid(p.nx, 2);
     k_fast_rows_inv<LY, TC><<<grid, LY / 16, sm, s>>>(gx, gy, p.nx, twy, fx, fy);

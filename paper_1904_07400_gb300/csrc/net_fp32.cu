@@ -1,0 +1,686 @@
+// FP32 force solve for grids whose sides are 1024, 2048 or 4096 cells, built around the
+// one-barrier register FFT network of fft_net.cuh and the data movement of sm_103a:
+//
+//  * pass A (rows): chunked register spline solve, packed real transform, unpack, and a
+//    TMA bulk-tensor store of the row into the tiled intermediate Z;
+//  * pass B (columns): chunked register spline solve, the zero-padded column transform as
+//    two half-length transforms (even and odd frequencies), both spectrum products and
+//    four inverse half-length transforms, with the spectra stored in the network's
+//    output order;
+//  * pass C (rows): TMA bulk-tensor load of one row of G, Hermitian repack, transform,
+//    crop and store.
+//
+// The padded transforms use the zero padding exactly (no length-2N transform is formed)
+// and the spectra use their parity in kx (half of each half table is stored).
+//
+// Intermediates Z, G_x, G_y: nx x hy complex values in two-column tiles, element
+// (row, ky) at [ky / 2][row][ky % 2].  For order 3, Z stores row i at position
+// (i % 16) * (nx / 16) + i / 16, so a column block's thread t reads its rows 16 t .. 16 t + 15
+// (the chunk its spline solve owns) with coalesced loads.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "fft_net.cuh"
+#include "tdg_internal.cuh"
+
+namespace tdg {
+namespace {
+
+using net::cf;
+using reg::pad;
+
+constexpr int kTW = 2;  // tile width of the intermediates
+
+// ---------------------------------------------------------------------------------------
+// Spline coefficients by the truncated tridiagonal solve (1/8)(c_{i-1} + 6 c_i + c_{i+1})
+// = s_i (c = 0 outside the line), line length 16 T, thread t owning the chunk
+// [16 t, 16 t + 16) in registers.
+//
+// Exact LU: y_0 = 8 s_0, y_i = 8 s_i - lam_{i-1} y_{i-1}; c_{n-1} = lam_{n-1} y_{n-1},
+// c_i = lam_i (y_i - c_{i+1}), lam_i = 1 / d_i, d_0 = 6, d_i = 6 - 1 / d_{i-1}.  lam_i
+// equals its limit lam = 3 - 2 sqrt 2 to float precision from i = 6 on.
+//
+// Each thread sweeps its chunk from zero in both directions (first chunk: exact lam_i).
+// The true values differ from the local ones by the homogeneous solutions driven by the
+// two chunk edges: c = c_local + Y h + C g, with Y = y at the end of the previous chunk,
+// C = c at the start of the next one, h the backward sweep of (-lam)^(r+1), and
+// g_r = (-lam)^(16-r).  Y and C are the neighbours' local values (their own corrections
+// are below lam^16 = 6e-13 relative), exchanged by shuffles and, across warps, through
+// shared memory with one barrier.
+// ---------------------------------------------------------------------------------------
+constexpr double kLamInf = 0.17157287525380990239662255158060;  // 3 - 2 sqrt 2
+
+__host__ __device__ constexpr double lam_exact(int i) {
+    double d = 6.0;
+    for (int k = 0; k < i; ++k) d = 6.0 - 1.0 / d;
+    return 1.0 / d;
+}
+
+__host__ __device__ constexpr double pow_neg_lam(int k) {
+    double r = 1.0;
+    for (int q = 0; q < k; ++q) r *= -kLamInf;
+    return r;
+}
+
+// h_r: backward local sweep of e_r = (-lam)^(r+1), r < 16
+__host__ __device__ constexpr double h_coef(int r) {
+    double c = kLamInf * pow_neg_lam(16);
+    for (int q = 14; q >= r; --q) c = kLamInf * (pow_neg_lam(q + 1) - c);
+    return c;
+}
+
+// the solve's constants, folded at compile time
+struct SolveTabs {
+    float h[16], g[16], lam[6];
+};
+__host__ __device__ constexpr SolveTabs make_solve_tabs() {
+    SolveTabs s{};
+    for (int r = 0; r < 16; ++r) {
+        s.h[r] = (float)h_coef(r);
+        s.g[r] = (float)pow_neg_lam(16 - r);
+    }
+    for (int i = 0; i < 6; ++i) s.lam[i] = (float)lam_exact(i);
+    return s;
+}
+
+__device__ __forceinline__ float vs(float a, float s) { return a * s; }
+__device__ __forceinline__ cf vs(cf a, float s) { return scl(a, s); }
+__device__ __forceinline__ float vfma(float a, float s, float b) { return fmaf(a, s, b); }
+__device__ __forceinline__ cf vfma(cf a, float s, cf b) { return mk(fmaf(a.x, s, b.x), fmaf(a.y, s, b.y)); }
+__device__ __forceinline__ float vzero(float) { return 0.f; }
+__device__ __forceinline__ cf vzero(cf) { return mk(0.f, 0.f); }
+__device__ __forceinline__ float shfl_up1(float a) { return __shfl_up_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ cf shfl_up1(cf a) {
+    return mk(__shfl_up_sync(0xffffffffu, a.x, 1), __shfl_up_sync(0xffffffffu, a.y, 1));
+}
+__device__ __forceinline__ float shfl_down1(float a) { return __shfl_down_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ cf shfl_down1(cf a) {
+    return mk(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
+}
+
+// x: the thread's chunk (in: s, out: c).  edge: 2 * (nthreads / 32) values of shared
+// memory.  Called by every thread of the block (one __syncthreads).
+template <typename V>
+__device__ __forceinline__ void solve_chunk(V* x, int t, int nthreads, V* edge) {
+    constexpr SolveTabs K = make_solve_tabs();
+    const float li = (float)kLamInf;
+    // forward sweep from zero (exact start on the first chunk)
+    x[0] = vs(x[0], 8.0f);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+        const float l = (t == 0 && r - 1 < 6) ? K.lam[r - 1] : li;
+        x[r] = vs(x[r], 8.0f) - vs(x[r - 1], l);
+    }
+    const V ylast = x[15];
+    // backward sweep from zero (lam_{n-1} = lam: exact on the last chunk)
+    x[15] = vs(x[15], li);
+#pragma unroll
+    for (int r = 14; r >= 0; --r) {
+        const float l = (t == 0 && r < 6) ? K.lam[r] : li;
+        x[r] = vs(x[r] - x[r + 1], l);
+    }
+    const V cfirst = x[0];
+    // neighbours' edge values
+    const int lane = t & 31, w = t >> 5, nw = nthreads >> 5;
+    V yprev = shfl_up1(ylast);
+    V cnext = shfl_down1(cfirst);
+    if (lane == 31) edge[w] = ylast;
+    if (lane == 0) edge[nw + w] = cfirst;
+    __syncthreads();
+    if (lane == 0) yprev = w > 0 ? edge[w - 1] : vzero(ylast);
+    if (lane == 31) cnext = w + 1 < nw ? edge[nw + w + 1] : vzero(ylast);
+    const V Y = t > 0 ? yprev : vzero(ylast);
+    const V C = t + 1 < nthreads ? vfma(ylast, K.h[0], cnext) : vzero(ylast);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) x[r] = vfma(C, K.g[r], vfma(Y, K.h[r], x[r]));
+}
+
+// ---------------------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) and mbarrier helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for phase `parity` of the barrier: false after about a second of naps
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(1000);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void flag_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+constexpr int kBox = 256;  // tile cells per TMA box (the box-dimension limit)
+
+// ---------------------------------------------------------------------------------------
+// Tables
+// ---------------------------------------------------------------------------------------
+// per-thread twiddle bases of the network: [0, T) W_L^perm(t), [T, 2T) W_{16R}^(t / 16)
+template <int L>
+__global__ void k_net_bases(cf* tab) {
+    constexpr int T = L / 16, R = L / 256;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    double s, c;
+    sincospi(-2.0 * (double)net::perm<L>(t) / (double)L, &s, &c);
+    tab[t] = mk((float)c, (float)s);
+    sincospi(-2.0 * (double)(t >> 4) / (double)(16 * R), &s, &c);
+    tab[T + t] = mk((float)c, (float)s);
+}
+
+// half spectra in the network's output order, per ky: the even half (X_e, kx = 2k) as
+// rows k_a < 8 of T entries (entry k_a T + t holds k = perm(t) + T k_a) then k = L/2 and a
+// pad entry; the odd half (X_o, kx = 2k + 1) as rows k_a < 8.  Values (s_x, s_y).
+template <int L>
+__global__ void k_net_spectra(const float* __restrict__ full, int hy, float2* __restrict__ half) {
+    constexpr int T = L / 16, HS = L / 2 + 2, Px = 2 * L;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)hy * 2 * HS) return;
+    const int ky = (int)(idx / (2 * HS));
+    const int rem = (int)(idx % (2 * HS));
+    const int h = rem / HS, q = rem % HS;
+    int kx = -1;
+    if (q < L / 2) kx = 2 * (net::perm<L>(q % T) + T * (q / T)) + h;
+    else if (q == L / 2 && h == 0) kx = L;
+    float2 v = make_float2(0.f, 0.f);
+    if (kx >= 0) {
+        v.x = full[(size_t)ky * Px + kx];
+        v.y = full[(size_t)hy * Px + (size_t)ky * Px + kx];
+    }
+    half[idx] = v;
+}
+
+__device__ __forceinline__ cf ld2(const cf* p) {
+    float2 v = *reinterpret_cast<const float2*>(p);
+    return mk(v.x, v.y);
+}
+
+// X = (Za + conj Zb)/2 - i w (Za - conj Zb)/2
+__device__ __forceinline__ cf unpack_r2c(cf za, cf zb, cf w) {
+    cf e = mk(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+    cf d = mk(0.5f * (za.x - zb.x), 0.5f * (za.y + zb.y));
+    cf wd = cmul(w, d);
+    return mk(e.x + wd.y, e.y - wd.x);
+}
+
+// Z = (Xa + conj Xb) + i conj(w) (Xa - conj Xb)
+__device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
+    cf e = mk(xa.x + xb.x, xa.y - xb.y);
+    cf d = mk(xa.x - xb.x, xa.y + xb.y);
+    cf wd = cmulc(d, w);
+    return mk(e.x - wd.y, e.y + wd.x);
+}
+
+// ---------------------------------------------------------------------------------------
+// pass A: one row i per block (T = L / 16 threads); row length L = ny, transformed as the
+// packed complex sequence z_n = s_2n + i s_2n+1 of length L (period 2L, upper half zero).
+// Shared memory: E = network buffer, later the row's cells for the TMA store; U = the
+// float row for the solve's transposition, later Z in padded natural order; edge.
+// ---------------------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(L / 16, 3)
+    k_net_rows(const float* __restrict__ sigma, int solve, int rowmap, int nx, const cf* __restrict__ nb,
+               const cf* __restrict__ tw, const __grid_constant__ CUtensorMap zmap, cf* __restrict__ z) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* E = reinterpret_cast<cf*>(smem_raw);
+    cf* U = E + BUF;
+    float* edge = reinterpret_cast<float*>(U + BUF);
+    const int t = threadIdx.x;
+    const int i = blockIdx.x;
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    cf v[16];
+    if (solve) {
+        // thread t owns s[16 t .. 16 t + 15]
+        const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * L) + 4 * t;
+        float x[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 f = src[q];
+            x[4 * q] = f.x;
+            x[4 * q + 1] = f.y;
+            x[4 * q + 2] = f.z;
+            x[4 * q + 3] = f.w;
+        }
+        solve_chunk<float>(x, t, T, edge);
+        // chunk -> natural-strided pairs through U (float index f at f + 4 (f / 32))
+        float* uf = reinterpret_cast<float*>(U);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4*>(uf + 16 * t + 4 * q + 4 * (t >> 1)) =
+                make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int n = t + T * c;
+            const float2 p = *reinterpret_cast<const float2*>(uf + 2 * n + 4 * (n >> 4));
+            v[c] = mk(p.x, p.y);
+        }
+    } else {
+        const float2* row = reinterpret_cast<const float2*>(sigma + (size_t)i * L);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float2 p = row[t + T * c];
+            v[c] = mk(p.x, p.y);
+        }
+    }
+#pragma unroll
+    for (int c = 8; c < 16; ++c) v[c] = mk(0.f, 0.f);
+    net::fwd<L>(v, E, bs, t);
+    // Z (network order) -> U, natural padded
+    const int pt = net::perm<L>(t);
+#pragma unroll
+    for (int ka = 0; ka < 16; ++ka) U[pad(pt + T * ka)] = v[ka];
+    const float znyq = v[0].x - v[0].y;  // X[L] (thread 0: v[0] = Z[0])
+    __syncthreads();
+    // cells p = t + T q: (X[2p], X[2p+1]) with X[k] = unpack(Z[k], Z[L-k], W_2L^k)
+    const cf w2t = reg::ld_tw(tw, 2 * t);  // W_2L^(2t)
+    const cf w1 = reg::ld_tw(tw, 1);       // W_2L
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int p = t + T * q;
+        const int k0 = 2 * p;
+        const cf wk0 = reg::mul_w16(w2t, q);  // W_2L^(2t + 2Tq), 2T = L / 8
+        const cf wk1 = cmul(wk0, w1);
+        const cf x0 = unpack_r2c(U[pad(k0)], U[pad((L - k0) & (L - 1))], wk0);
+        const cf x1 = unpack_r2c(U[pad(k0 + 1)], U[pad(L - k0 - 1)], wk1);
+        *reinterpret_cast<float4*>(E + k0) = make_float4(x0.x, x0.y, x1.x, x1.y);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (t == 0) {
+        const int rp = rowmap ? (i & 15) * (nx >> 4) + (i >> 4) : i;
+#pragma unroll 1
+        for (int b = 0; b < L / 2 / kBox; ++b) tma_store_3d(&zmap, 0, rp, b * kBox, E + 2 * b * kBox);
+        bulk_commit();
+        z[(size_t)(L / 2) * nx * kTW + (size_t)rp * kTW] = mk(znyq, 0.f);
+        bulk_wait_all();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// pass C: one row i of one component (blockIdx.y) per block.  The row's L/2 tile cells
+// arrive by TMA; the Nyquist cell by a plain load.  Shared memory: S = the row (L + 2
+// complex), later the cropped output in padded natural order; E = network buffer; bar.
+// ---------------------------------------------------------------------------------------
+template <int L>
+constexpr int inv_e_offset() {
+    return (((L + 2) * 8 + 1023) / 1024) * 1024;  // bytes
+}
+
+template <int L>
+__global__ void __launch_bounds__(L / 16, 3)
+    k_net_rows_inv(const __grid_constant__ CUtensorMap gmap, const cf* __restrict__ g0, const cf* __restrict__ g1,
+                   int nx, const cf* __restrict__ nb, const cf* __restrict__ tw, float* __restrict__ f0,
+                   float* __restrict__ f1, int* __restrict__ err) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* S = reinterpret_cast<cf*>(smem_raw);
+    cf* E = reinterpret_cast<cf*>(smem_raw + inv_e_offset<L>());
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(E + BUF);
+    const int t = threadIdx.x;
+    const int i = blockIdx.x, comp = blockIdx.y;
+    if (t == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (t == 0) {
+        mbar_expect_tx(bar, (unsigned)(L * sizeof(cf)));
+#pragma unroll 1
+        for (int b = 0; b < L / 2 / kBox; ++b) tma_load_4d(S + 2 * b * kBox, &gmap, 0, i, b * kBox, comp, bar);
+        const cf* g = comp ? g1 : g0;
+        S[L] = ld2(g + (size_t)(L / 2) * nx * kTW + (size_t)i * kTW);  // read back by this thread only
+    }
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    const cf wt = reg::ld_tw(tw, t);
+    const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
+    if (!ok) {
+        // the row never arrived: report, give the copy one more bounded wait, leave
+        if (t == 0) flag_error(err, TDG_ERR_TIMEOUT);
+        mbar_wait(bar, 0);
+        return;
+    }
+    // conj of the Hermitian repack, natural strided: the inverse transform is
+    // conj(fwd(conj(Z)))
+    cf v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = t + T * r;
+        v[r] = conjg(pack_c2r(S[k], S[L - k], reg::twist(wt, r)));
+    }
+    net::fwd<L>(v, E, bs, t);
+    // keep n = perm(t) + T ka < L/2, i.e. ka < 8; transpose back through S
+    const int pt = net::perm<L>(t);
+#pragma unroll
+    for (int ka = 0; ka < 8; ++ka) S[pad(pt + T * ka)] = conjg(v[ka]);
+    __syncthreads();
+    float2* out = reinterpret_cast<float2*>((comp ? f1 : f0) + (size_t)i * L);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const cf o = S[pad(t + T * c)];
+        out[t + T * c] = make_float2(o.x, o.y);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// pass B: one frequency column ky per block, column length L = nx.
+// Spectra (k_net_spectra): per ky the even half then the odd half, HS = L/2 + 2 entries
+// each, in network order.  The products are conj(i s X) (the inverse transforms run as
+// conj(inv_t(conj(.)))).  For fixed ky, s_x is odd and s_y even in kx, so entries past
+// the middle of a half come from the mirrored entry, with s_x negated.
+// ---------------------------------------------------------------------------------------
+template <int L, int H>
+__device__ __forceinline__ void spec_products(cf* wx, cf* v, const float2* __restrict__ sh, int t, int pt,
+                                              int tm) {
+    constexpr int T = L / 16;
+#pragma unroll
+    for (int ka = 0; ka < 16; ++ka) {
+        int idx;
+        bool direct;
+        if (ka < 8) {
+            idx = ka * T + t;
+            direct = true;
+        } else if (H == 0 && pt == 0) {
+            idx = (16 - ka) * T;  // k = T ka, mirror T (16 - ka); ka = 8 is the middle itself
+            direct = ka == 8;
+        } else {
+            idx = (15 - ka) * T + tm;
+            direct = false;
+        }
+        const float2 q = __ldg(sh + idx);
+        const float sx = direct ? q.x : -q.x;
+        const float sy = q.y;
+        const cf x = v[ka];
+        wx[ka] = mk(-sx * x.y, -sx * x.x);
+        v[ka] = mk(-sy * x.y, -sy * x.x);
+    }
+}
+
+template <int L>
+constexpr size_t cols_smem_bytes() {
+    constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
+    return (size_t)(2 * BUF + 16 * T) * sizeof(cf) + 2 * (T / 32) * sizeof(cf);
+}
+
+template <int L>
+__global__ void __launch_bounds__(L / 16, 2)
+    k_net_cols(const cf* __restrict__ z, int solve, const cf* __restrict__ nb, const cf* __restrict__ tw,
+               const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    constexpr int HS = L / 2 + 2;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
+    cf* xb = E + BUF;                         // the column (padded natural), later the even y result
+    cf* sb = xb + BUF;                        // the even x result, [r][t]
+    cf* edge = sb + 16 * T;
+    const int t = threadIdx.x;
+    const int ky = blockIdx.x;
+    const int tile = ky >> 1, c = ky & 1;
+    const size_t slab = (size_t)L * kTW;
+    const cf* zc = z + (size_t)tile * slab + c;
+    const float2* se = spec + (size_t)ky * 2 * HS;
+    const float2* so = se + HS;
+    if (t == 0) {
+        // the column's spectra are read after the solve and the first transform
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(se), "r"((unsigned)(2 * HS * sizeof(float2)))
+                     : "memory");
+    }
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    if (solve) {
+        cf x[16];  // rows 16 t + r, stored at r T + t
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = ld2(zc + (size_t)(r * T + t) * kTW);
+        solve_chunk<cf>(x, t, T, edge);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = x[r];
+        __syncthreads();
+    } else {
+        cf x[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = ld2(zc + (size_t)(t + r * T) * kTW);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = x[r];  // own positions
+    }
+    const int pt = net::perm<L>(t);
+    const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);  // even half: mirror of k is L - k
+    const int to = net::perm_inv<L>(T - 1 - pt);             // odd half: mirror of k is L - 1 - k
+    cf v[16], w[16];
+    // even frequencies X_e = FFT_L(x)
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
+    net::fwd<L>(v, E, bs, t);
+    spec_products<L, 0>(w, v, se, t, pt, te);
+    net::inv_t<L>(w, E, bs, t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sb[r * T + t] = w[r];
+    __syncthreads();
+    net::inv_t<L>(v, E, bs, t);
+    // odd frequencies: X_o = FFT_L(x_n W_2L^n); park the even y result in the column's place
+    {
+        const cf wt = reg::ld_tw(tw, t);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            w[r] = cmul(xb[pad(n)], reg::twist(wt, r));
+            xb[pad(n)] = v[r];
+        }
+    }
+    __syncthreads();
+    net::fwd<L>(w, E, bs, t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = w[r];
+    spec_products<L, 1>(w, v, so, t, pt, to);
+    net::inv_t<L>(w, E, bs, t);
+    // G = conj(u_even + W_2L^n u_odd): W_2L^n as conj of W_2L^-n (table entry 2L - t)
+    const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
+    cf* gxc = gx + (size_t)tile * slab + c;
+    cf* gyc = gy + (size_t)tile * slab + c;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int n = t + r * T;
+        gxc[(size_t)n * kTW] = conjg(sb[r * T + t] + cmulc(w[r], reg::untwist(wtc, r)));
+    }
+    __syncthreads();
+    net::inv_t<L>(v, E, bs, t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int n = t + r * T;
+        gyc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+// the tiled intermediate(s) as a tensor of floats {4 (one tile cell), nx rows, ntile cells,
+// ncomp}: strides 16 B, nx * 16 B, comp_bytes; box {4, 1, kBox, 1}
+cudaError_t encode_tiles(CUtensorMap* map, void* base, int nx, int ntile, int ncomp, size_t comp_bytes) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint32_t rank = ncomp > 1 ? 4 : 3;
+    cuuint64_t dims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ntile, (cuuint64_t)ncomp};
+    cuuint64_t strides[3] = {16, (cuuint64_t)nx * 16, (cuuint64_t)comp_bytes};
+    cuuint32_t box[4] = {4, 1, (cuuint32_t)kBox, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int L>
+size_t rows_bytes() {
+    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 2 * (L / 16 / 32) * sizeof(float);
+}
+
+template <int L>
+size_t inv_bytes() {
+    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16;
+}
+
+// bases tables of the plan: x axis first (2 T_x values), then y (2 T_y)
+const cf* bases_x(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw); }
+const cf* bases_y(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw) + p.nx / 8; }
+
+template <int LX, int LY>
+cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+    const int hy = p.hy;
+    const int ntile = (hy + kTW - 1) / kTW;
+    const size_t n_el = (size_t)ntile * p.nx * kTW;
+    cf* z = reinterpret_cast<cf*>(work);
+    cf* gx = z + n_el;
+    cf* gy = gx + n_el;
+    const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
+    const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
+    const int solve = p.order == 3;
+    cudaError_t e;
+    CUtensorMap zmap, gmap;
+    if ((e = encode_tiles(&zmap, z, p.nx, ntile, 1, 0))) return e;
+    if ((e = encode_tiles(&gmap, gx, p.nx, ntile, 2, n_el * sizeof(cf)))) return e;
+
+    size_t sm = rows_bytes<LY>();
+    if ((e = set_smem(k_net_rows<LY>, sm))) return e;
+    mark(p, 0, s);
+    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, solve, solve, p.nx, bases_y(p), twy, zmap, z);
+    if ((e = cudaGetLastError())) return e;
+    mark(p, 1, s);
+    sm = cols_smem_bytes<LX>();
+    if ((e = set_smem(k_net_cols<LX>, sm))) return e;
+    k_net_cols<LX><<<hy, LX / 16, sm, s>>>(z, solve, bases_x(p), twx, reinterpret_cast<const float2*>(p.spec_half),
+                                           gx, gy);
+    if ((e = cudaGetLastError())) return e;
+    mark(p, 2, s);
+    sm = inv_bytes<LY>();
+    if ((e = set_smem(k_net_rows_inv<LY>, sm))) return e;
+    k_net_rows_inv<LY><<<dim3(p.nx, 2), LY / 16, sm, s>>>(gmap, gx, gy, p.nx, bases_y(p), twy, fx, fy, p.err);
+    e = cudaGetLastError();
+    mark(p, 3, s);
+    return e;
+}
+
+template <int LX>
+cudaError_t run_net_x(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+    switch (p.ny) {
+        case 1024: return run_net<LX, 1024>(p, sigma, fx, fy, work, s);
+        case 2048: return run_net<LX, 2048>(p, sigma, fx, fy, work, s);
+        default: return run_net<LX, 4096>(p, sigma, fx, fy, work, s);
+    }
+}
+
+template <int L>
+cudaError_t build_axis(const Plan& p, cf* tab, cudaStream_t s) {
+    k_net_bases<L><<<(L / 16 + 255) / 256, 256, 0, s>>>(tab);
+    return cudaGetLastError();
+}
+
+cudaError_t build_bases(const Plan& p, cf* tab, int n, cudaStream_t s) {
+    switch (n) {
+        case 1024: return build_axis<1024>(p, tab, s);
+        case 2048: return build_axis<2048>(p, tab, s);
+        default: return build_axis<4096>(p, tab, s);
+    }
+}
+
+template <int L>
+cudaError_t spectra_axis(const Plan& p, cudaStream_t s) {
+    const long total = (long)p.hy * 2 * (L / 2 + 2);
+    k_net_spectra<L><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float*>(p.spec), p.hy,
+                                                                        reinterpret_cast<float2*>(p.spec_half));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool net_fp32_eligible(const Plan& p) {
+    return p.prec == TDG_FP32 && fast_fp32_eligible(p) && encode_fn() != nullptr;
+}
+
+size_t net_fp32_table_bytes(const Plan& p) { return (size_t)(p.nx / 8 + p.ny / 8) * sizeof(cf); }
+
+cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
+    cudaError_t e;
+    cf* tab = reinterpret_cast<cf*>(p.net_tw);
+    if ((e = build_bases(p, tab, p.nx, s))) return e;
+    if ((e = build_bases(p, tab + p.nx / 8, p.ny, s))) return e;
+    switch (p.nx) {
+        case 1024: return spectra_axis<1024>(p, s);
+        case 2048: return spectra_axis<2048>(p, s);
+        default: return spectra_axis<4096>(p, s);
+    }
+}
+
+cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
+                               cudaStream_t s) {
+    switch (p.nx) {
+        case 1024: return run_net_x<1024>(p, sigma, fx, fy, work, s);
+        case 2048: return run_net_x<2048>(p, sigma, fx, fy, work, s);
+        default: return run_net_x<4096>(p, sigma, fx, fy, work, s);
+    }
+}
+
+}  // namespace tdg

@@ -196,6 +196,7 @@ template <typename T>
 cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* work, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         // register-resident transforms for sides of 1024, 2048 or 4096 cells
+        if (p.spec_half && p.net_tw) return launch_forward_net(p, sigma, fx, fy, work, s);
         if (p.spec_half && fast_fp32_eligible(p)) return launch_forward_fast(p, sigma, fx, fy, work, s);
     }
     const Tiled t = tiled_of<T>(p, p.nx);

@@ -72,6 +72,7 @@ struct Plan {
     void* tw_y;            // twiddles exp(-2 pi i k / P_y), k < P_y
     void* spec;            // spectra s_x, s_y: 2 x hy x P_x reals, layout [c][ky][kx]
     void* spec_half;       // FP32 fast path: half spectra [ky][even|odd][k] of (s_x, s_y)
+    void* net_tw;          // FP32 network path: per-thread twiddle bases, x axis then y
     double* wq;            // FP64 quarter tables w^x, w^y: 2 x nx x ny (kept for tests)
     void* work;            // workspace (plan-owned or caller-owned)
     size_t work_bytes;
@@ -111,6 +112,11 @@ size_t fast_fp32_spec_bytes(const Plan& p);
 cudaError_t launch_half_spectra(const Plan& p, cudaStream_t s);
 cudaError_t launch_forward_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                 cudaStream_t s);
+bool net_fp32_eligible(const Plan& p);
+size_t net_fp32_table_bytes(const Plan& p);
+cudaError_t launch_net_tables(const Plan& p, cudaStream_t s);
+cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_adjoint(const Plan& p, const T* gx, const T* gy, T* gsig, void* work,
                            cudaStream_t s);
