@@ -904,10 +904,24 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
 //   x W_2L^n -> B;  X_e = fwd(x);  y product -> A;  inv(x product) -> xb (the column is
 //   dead);  A -> inv(y product) -> A;  B -> X_o = fwd;  y product -> B;
 //   G_x = conj(xb + W^n inv(x product));  B -> G_y = conj(A + W^n inv(y product)).
+#ifndef TDG_COLS_DB
+#define TDG_COLS_DB 0
+#endif
+// 1: for 4096-cell columns the even x result also goes to tensor memory and the column
+// shares the network buffer (one shared buffer per block, the rest left to L1)
+#ifndef TDG_COLS_SLIM
+#define TDG_COLS_SLIM 1
+#endif
+
+template <int L>
+constexpr bool cols_slim() {
+    return TDG_COLS_SLIM && !TDG_COLS_DB && L == 4096;
+}
+
 template <int L>
 constexpr size_t cols_tm_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16;
+    return (size_t)((cols_slim<L>() ? 1 : 2 + TDG_COLS_DB) * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16;
 }
 
 #ifndef TDG_COLS_TM_MINB
@@ -921,11 +935,18 @@ __global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     constexpr int HS = L / 2 + 2;
-    constexpr unsigned kCols = T > 128 ? 128 : 64;  // warps w and w + 4 share a lane quarter
+    constexpr bool kSlim = cols_slim<L>();
+    // warps w and w + 4 share a lane quarter; slots of 32 columns: A, B (and C when slim)
+    constexpr unsigned kCols = kSlim ? 256 : (T > 128 ? 128 : 64);
+    constexpr unsigned kWarpCols = kSlim ? 128 : 64;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
-    cf* xb = E + BUF;                         // the column (padded natural), later the even x result
-    cf* edge = xb + BUF;
+    // the column (padded natural), later the even x result; slim: the column shares E
+    cf* xb = kSlim ? E : E + BUF;
+    // second network buffer: transforms alternate E, E2 wherever two in a row would
+    // otherwise need a barrier between them (inv_t then inv_t, inv_t then fwd)
+    cf* E2 = TDG_COLS_DB ? xb + BUF : E;
+    cf* edge = kSlim ? E + BUF : xb + (1 + TDG_COLS_DB) * BUF;
     unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
     const int t = threadIdx.x;
     if (t < 32) tmem_alloc(tslot, kCols);
@@ -952,6 +973,7 @@ __global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
         tmem_fence_after();
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
+        if (kSlim) __syncthreads();  // the column is read before fwd writes the buffer
     } else {
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = ld2(zc + (size_t)(t + r * T) * kTW);
@@ -959,8 +981,9 @@ __global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
         __syncthreads();
         tmem_fence_after();
     }
-    const unsigned tA = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + (unsigned)(64 * (t >> 7));
+    const unsigned tA = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + kWarpCols * (unsigned)(t >> 7);
     const unsigned tB = tA + 32;
+    const unsigned tC = tA + 64;  // slim only
     const int pt = net::perm<L>(t);
     const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);
     const int to = net::perm_inv<L>(T - 1 - pt);
@@ -979,29 +1002,47 @@ __global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
     net::fwd<L>(v, E, bs, t);
     spec_products_tm<L, 0>(v, se, t, pt, te, tA);
     net::inv_t<L>(v, E, bs, t);
-    // every thread has read its column values from xb before fwd's barrier: reuse it
+    if (kSlim) {
+        tmem_store16(tC, v);
+    } else {
+        // every thread has read its column values from xb before fwd's barrier: reuse it
 #pragma unroll
-    for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];  // own slots
+        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];  // own slots
+    }
     tmem_load16(tA, v);
-    __syncthreads();
-    net::inv_t<L>(v, E, bs, t);
+    if (!TDG_COLS_DB) __syncthreads();
+    net::inv_t<L>(v, E2, bs, t);
     tmem_store16(tA, v);  // even y result
     tmem_load16(tB, v);   // x W_2L^n
-    __syncthreads();
+    if (!TDG_COLS_DB) __syncthreads();
     net::fwd<L>(v, E, bs, t);
     spec_products_tm<L, 1>(v, so, t, pt, to, tB);
     net::inv_t<L>(v, E, bs, t);
     const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
     cf* gxc = gx + (size_t)tile * slab + c;
     cf* gyc = gy + (size_t)tile * slab + c;
+    if (kSlim) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int n = t + r * T;
-        gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+        for (int g = 0; g < 4; ++g) {
+            cf ex[4];
+            tmem_load4(tC + 8 * g, ex);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = 4 * g + e;
+                const int n = t + r * T;
+                gxc[(size_t)n * kTW] = conjg(ex[e] + cmulc(v[r], reg::untwist(wtc, r)));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+        }
     }
     tmem_load16(tB, v);
-    __syncthreads();
-    net::inv_t<L>(v, E, bs, t);
+    if (!TDG_COLS_DB) __syncthreads();
+    net::inv_t<L>(v, E2, bs, t);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         cf ey[4];
