@@ -27,10 +27,6 @@ using reg::pad;
 
 constexpr int kTW = 2;  // tile width of the intermediates
 
-// 1: the row kernels give each transform's two exchanges separate shared buffers
-#ifndef TDG_DB
-#define TDG_DB 0
-#endif
 
 // ---------------------------------------------------------------------------------------
 // truncated tridiagonal solve (1/8)(c_{i-1} + 6 c_i + c_{i+1}) = s_i on one line held in
@@ -249,13 +245,7 @@ __global__ void __launch_bounds__(L / 16, TC ? 2 : 3) k_fast_rows(const float* _
     }
 #pragma unroll
     for (int r = 8; r < 16; ++r) v[r] = mk(0.f, 0.f);
-    if constexpr (TDG_DB && !TC) {
-        // the second exchange buffer overlays the row buffer and lam: every thread has
-        // read them before the first exchange's barrier
-        reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K, reinterpret_cast<cf*>(rbuf));
-    } else {
-        reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
-    }
+    reg::fft<L, R1, TC>(v, eb, tb, t, ws, &K);
     // unpack the real transform: X[k] from Z[k] and Z[L - k]
 #pragma unroll
     for (int r = 0; r < 16; ++r) eb[pad(t + r * T)] = v[r];
@@ -509,8 +499,7 @@ __global__ void __launch_bounds__(L / 16, TC ? 2 : 3) k_fast_rows_inv(const cf* 
         v[r] = pack_c2r(xb[pad(k)], xb[pad(L - k)], reg::twist(wt, r));
     }
     __syncthreads();
-    if constexpr (TDG_DB && !TC) reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K, xb + LP);
-    else reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K);
+    reg::ifft<L, R1, TC>(v, xb, tb, t, ws, &K);
     float2* out = reinterpret_cast<float2*>(f + (size_t)i * L);
 #pragma unroll
     for (int r = 0; r < 8; ++r) out[t + r * T] = make_float2(v[r].x, v[r].y);
@@ -546,7 +535,6 @@ size_t rows_smem(int solve, bool tc) {
     constexpr int LP = L + L / 16 + 16;
     // the order-3 row buffer is always reserved so the TC scratch has a fixed offset
     (void)solve;
-    if (TDG_DB && !tc) return 2 * LP * sizeof(cf);
     return LP * sizeof(cf) + LP * sizeof(float) + kLam * sizeof(float) + tc_scratch<L>(tc);
 }
 
@@ -559,21 +547,12 @@ size_t cols_smem(bool tc) {
 template <int L>
 size_t inv_smem(bool tc) {
     constexpr int LP = L + L / 16 + 16;
-    if (TDG_DB && !tc) return 2 * LP * sizeof(cf);
     return LP * sizeof(cf) + tc_scratch<L>(tc);
 }
 
-#ifndef TDG_CARVE
-#define TDG_CARVE 0
-#endif
-
-// dynamic shared memory of a kernel; with TDG_CARVE the whole unified L1 / shared array
-// is requested as shared memory, so the occupancy the shared size allows is reached
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e || !TDG_CARVE) return e;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int LX, int LY, bool TC>

@@ -98,9 +98,29 @@ __device__ __forceinline__ void tw3(cf* v, cf b3) {
     reg::apply_powers<16>(v, b3, w4, csq(w4));
 }
 
-// forward DFT, NS in, SP out
+// twiddle providers of the network: Bases forms the powers from the two bases at every
+// stage; a kernel may pass any type with apply2(v) / apply3(v) (e.g. powers kept in
+// tensor memory)
 template <int L>
-__device__ __forceinline__ void fwd(cf* v, cf* buf, const Bases& bs, int t) {
+struct GenTw {
+    Bases b;
+    __device__ __forceinline__ void apply2(cf* v) const { tw2<L>(v, b.b2); }
+    __device__ __forceinline__ void apply3(cf* v) const { tw3(v, b.b3); }
+};
+
+// the 16 stage-2 factors (group m, b at v[m R + b]) and the 16 stage-3 factors (v[a]) of
+// thread t, for kernels that keep them
+template <int L>
+__device__ __forceinline__ void stage_factors(const Bases& bs, cf* f2, cf* f3) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f2[i] = f3[i] = mk(1.f, 0.f);
+    tw2<L>(f2, bs.b2);
+    tw3(f3, bs.b3);
+}
+
+// forward DFT, NS in, SP out
+template <int L, typename TW>
+__device__ __forceinline__ void fwd_p(cf* v, cf* buf, const TW& tw, int t) {
     constexpr int R = Cfg<L>::R, NM = Cfg<L>::NM;
     reg::dft16(v);
 #pragma unroll
@@ -112,7 +132,7 @@ __device__ __forceinline__ void fwd(cf* v, cf* buf, const Bases& bs, int t) {
     for (int m = 0; m < NM; ++m)
 #pragma unroll
         for (int b = 0; b < R; ++b) v[m * R + b] = slab[m * 16 * R + b * 16 + a];
-    tw2<L>(v, bs.b2);
+    tw.apply2(v);
     reg::butterflies<R>(v);
     __syncwarp();
 #pragma unroll
@@ -120,17 +140,22 @@ __device__ __forceinline__ void fwd(cf* v, cf* buf, const Bases& bs, int t) {
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = slab[a * 17 + i];
-    tw3(v, bs.b3);
+    tw.apply3(v);
     reg::dft16(v);
+}
+
+template <int L>
+__device__ __forceinline__ void fwd(cf* v, cf* buf, const Bases& bs, int t) {
+    fwd_p<L>(v, buf, GenTw<L>{bs}, t);
 }
 
 // transposed network, SP in, NS out (forward kernels): the unnormalised inverse DFT is
 // conj(inv_t(conj(X)))
-template <int L>
-__device__ __forceinline__ void inv_t(cf* v, cf* buf, const Bases& bs, int t) {
+template <int L, typename TW>
+__device__ __forceinline__ void inv_t_p(cf* v, cf* buf, const TW& tw, int t) {
     constexpr int R = Cfg<L>::R, NM = Cfg<L>::NM;
     reg::dft16(v);
-    tw3(v, bs.b3);
+    tw.apply3(v);
     const int a = t & 15;
     cf* slab = buf + (t >> 4) * 272;
     __syncwarp();  // a preceding fwd() on this buffer may still read the slab
@@ -140,7 +165,7 @@ __device__ __forceinline__ void inv_t(cf* v, cf* buf, const Bases& bs, int t) {
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = slab[s * 17 + a];
     reg::butterflies<R>(v);
-    tw2<L>(v, bs.b2);
+    tw.apply2(v);
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < NM; ++m)
@@ -150,6 +175,11 @@ __device__ __forceinline__ void inv_t(cf* v, cf* buf, const Bases& bs, int t) {
 #pragma unroll
     for (int kc = 0; kc < 16; ++kc) v[kc] = buf[(kc % R) * 272 + (kc / R) * 16 * R + t];
     reg::dft16(v);
+}
+
+template <int L>
+__device__ __forceinline__ void inv_t(cf* v, cf* buf, const Bases& bs, int t) {
+    inv_t_p<L>(v, buf, GenTw<L>{bs}, t);
 }
 
 }  // namespace net

@@ -237,7 +237,7 @@ __device__ __forceinline__ void butterflies(cf* v, cf* ws = nullptr, const TcCon
 
 // One exchange: registers (outputs of a stage of radix RA with stride NSA) -> shared ->
 // registers (inputs of the next stage of radix RB).  tw: W_L^m at tw[m * TS].
-template <int L, int RA, int NSA, int RB, bool TRAIL = true>
+template <int L, int RA, int NSA, int RB>
 __device__ __forceinline__ void exchange(cf* v, cf* buf, int t) {
     constexpr int T = L / 16;
     constexpr int BA = 16 / RA;
@@ -256,7 +256,7 @@ __device__ __forceinline__ void exchange(cf* v, cf* buf, int t) {
 #pragma unroll
         for (int r = 0; r < RB; ++r) v[b * RB + r] = buf[pad(j + r * (L / RB))];
     }
-    if constexpr (TRAIL) __syncthreads();
+    __syncthreads();
 }
 
 // exp(-2 pi i r / 32), r < 32: the factors W_2L^(r T) = W_32^r of the per-element twists
@@ -375,34 +375,26 @@ __device__ __forceinline__ cf untwist(cf wtc, int r) { return cmulc(wtc, w32(r))
 // shared buffer (L + L/16 values).  tb: the thread's twiddle bases (load_tw_base).
 // With TC, every radix-16 stage runs on the tensor cores (ws: the warp's scratch, K: the
 // lane's DFT_16 fragments); other radices stay on the FP32 pipes.
-//
-// With a second buffer buf2, the second exchange goes through buf2 and neither exchange
-// needs its trailing barrier: the next write into buf (the next transform's first
-// exchange) comes after this transform's second barrier, and the next write into buf2
-// after the next transform's first barrier.  The caller keeps both buffers for the
-// transforms alone between its own barriers.
 template <int L, int R1, bool TC = false>
 __device__ __forceinline__ void fft(cf* v, cf* buf, const TwBase<L, R1>& tb, int t, cf* ws = nullptr,
-                                    const TcConst* K = nullptr, cf* buf2 = nullptr) {
+                                    const TcConst* K = nullptr) {
     static_assert(16 * R1 * 16 == L, "L = 16 * R1 * 16");
     butterflies<16, TC>(v, ws, K);
-    if (buf2) exchange<L, 16, 1, R1, false>(v, buf, t);
-    else exchange<L, 16, 1, R1>(v, buf, t);
+    exchange<L, 16, 1, R1>(v, buf, t);
 #pragma unroll
     for (int q = 0; q < TwBase<L, R1>::B1; ++q) apply_powers<R1>(v + q * R1, tb.m1[q], tb.m4[q], tb.m8[q]);
     butterflies<R1, TC>(v, ws, K);
-    if (buf2) exchange<L, R1, 16, 16, false>(v, buf2, t);
-    else exchange<L, R1, 16, 16>(v, buf, t);
+    exchange<L, R1, 16, 16>(v, buf, t);
     apply_powers<16>(v, tb.l1, tb.l4, tb.l8);
     butterflies<16, TC>(v, ws, K);
 }
 
 template <int L, int R1, bool TC = false>
 __device__ __forceinline__ void ifft(cf* v, cf* buf, const TwBase<L, R1>& tb, int t, cf* ws = nullptr,
-                                     const TcConst* K = nullptr, cf* buf2 = nullptr) {
+                                     const TcConst* K = nullptr) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
-    fft<L, R1, TC>(v, buf, tb, t, ws, K, buf2);
+    fft<L, R1, TC>(v, buf, tb, t, ws, K);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
 }

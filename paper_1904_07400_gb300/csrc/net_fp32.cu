@@ -33,15 +33,6 @@ using reg::pad;
 
 constexpr int kTW = 2;  // tile width of the intermediates
 
-#ifndef TDG_INV_PERSIST
-#define TDG_INV_PERSIST 1
-#endif
-#ifndef TDG_ROWS_PERSIST
-#define TDG_ROWS_PERSIST 0
-#endif
-#ifndef TDG_COLS_SWAP
-#define TDG_COLS_SWAP 3
-#endif
 
 // ---------------------------------------------------------------------------------------
 // Spline coefficients by the truncated tridiagonal solve (1/8)(c_{i-1} + 6 c_i + c_{i+1})
@@ -221,11 +212,6 @@ __device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {  
 }
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ unsigned tmem_thread_addr(unsigned base, int t) {
-    const int w = t >> 5;
-    return base + ((unsigned)(32 * (w & 3)) << 16) + (unsigned)(32 * (w >> 2));
-}
 
 __device__ __forceinline__ void tmem_store16(unsigned a, const cf* v) {
     asm volatile(
@@ -419,175 +405,24 @@ __global__ void __launch_bounds__(L / 16, 3)
     }
 }
 
-// Persistent form of pass A (order 3): each block walks rows b, b + G, ...; every thread
-// prefetches its chunk of the next row by cp.async into its own slots of P as soon as it
-// has taken the current chunk, so the load overlaps the whole row's work.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-template <int L>
-constexpr size_t rows_p_bytes() {
-    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + (L + L / 8) * sizeof(float) +
-           2 * (L / 16 / 32) * sizeof(float);
-}
-
-template <int L>
-__global__ void __launch_bounds__(L / 16, 2)
-    k_net_rows_p(const float* __restrict__ sigma, int nrows, int nx, const cf* __restrict__ nb,
-                 const cf* __restrict__ tw, const __grid_constant__ CUtensorMap zmap, cf* __restrict__ z) {
-    constexpr int T = L / 16;
-    constexpr int BUF = net::Cfg<L>::BUF;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cf* E = reinterpret_cast<cf*>(smem_raw);
-    cf* U = E + BUF;
-    float* P = reinterpret_cast<float*>(U + BUF);  // L + L/8 floats: the prefetched chunks
-    float* edge = P + L + L / 8;
-    const int t = threadIdx.x;
-    int i = blockIdx.x;
-    if (i >= nrows) return;
-    float* mine = P + 16 * t + 4 * (t >> 1);  // this thread's padded chunk slots
-    auto prefetch = [&](int row) {
-        const float* src = sigma + (size_t)row * L + 16 * t;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cp_async16(mine + 4 * q, src + 4 * q);
-        cp_async_commit();
-    };
-    prefetch(i);
-    const net::Bases bs = net::load_bases<L>(nb, t);
-    const cf w2t = reg::ld_tw(tw, 2 * t);
-    const cf w1 = reg::ld_tw(tw, 1);
-    const int pt = net::perm<L>(t);
-    for (; i < nrows; i += gridDim.x) {
-        float x[16];
-        cp_async_wait_all();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 f = *reinterpret_cast<const float4*>(mine + 4 * q);
-            x[4 * q] = f.x;
-            x[4 * q + 1] = f.y;
-            x[4 * q + 2] = f.z;
-            x[4 * q + 3] = f.w;
-        }
-        if (i + (int)gridDim.x < nrows) prefetch(i + gridDim.x);
-        // the previous row's TMA store must have read E before anyone writes it again
-        if (t == 0) bulk_wait_read();
-        solve_chunk<float>(x, t, T, edge);
-        float* uf = reinterpret_cast<float*>(U);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<float4*>(uf + 16 * t + 4 * q + 4 * (t >> 1)) =
-                make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-        __syncthreads();
-        cf v[16];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int n = t + T * c;
-            const float2 p = *reinterpret_cast<const float2*>(uf + 2 * n + 4 * (n >> 4));
-            v[c] = mk(p.x, p.y);
-        }
-#pragma unroll
-        for (int c = 8; c < 16; ++c) v[c] = mk(0.f, 0.f);
-        net::fwd<L>(v, E, bs, t);
-#pragma unroll
-        for (int ka = 0; ka < 16; ++ka) U[pad(pt + T * ka)] = v[ka];
-        const float znyq = v[0].x - v[0].y;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int p = t + T * q;
-            const int k0 = 2 * p;
-            const cf wk0 = reg::mul_w16(w2t, q);
-            const cf wk1 = cmul(wk0, w1);
-            const cf x0 = unpack_r2c(U[pad(k0)], U[pad((L - k0) & (L - 1))], wk0);
-            const cf x1 = unpack_r2c(U[pad(k0 + 1)], U[pad(L - k0 - 1)], wk1);
-            *reinterpret_cast<float4*>(E + k0) = make_float4(x0.x, x0.y, x1.x, x1.y);
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (t == 0) {
-            const int rp = (i & 15) * (nx >> 4) + (i >> 4);
-#pragma unroll 1
-            for (int b = 0; b < L / 2 / kBox; ++b) tma_store_3d(&zmap, 0, rp, b * kBox, E + 2 * b * kBox);
-            bulk_commit();
-            z[(size_t)(L / 2) * nx * kTW + (size_t)rp * kTW] = mk(znyq, 0.f);
-        }
-    }
-    if (t == 0) bulk_wait_read();
-}
-
 // ---------------------------------------------------------------------------------------
-// pass C: one row i of one component (blockIdx.y) per block.  The row's L/2 tile cells
-// arrive by TMA; the Nyquist cell by a plain load.  Shared memory: S = the row (L + 2
-// complex), later the cropped output in padded natural order; E = network buffer; bar.
+// pass C: rows i of one component at a time.  A row's L/2 tile cells arrive by TMA, its
+// Nyquist cell by a plain load.  Shared memory: S = the row (L + 2 complex values),
+// E = network buffer, bar = the row's mbarrier.
 // ---------------------------------------------------------------------------------------
 template <int L>
 constexpr int inv_e_offset() {
     return (((L + 2) * 8 + 1023) / 1024) * 1024;  // bytes
 }
 
-template <int L>
-__global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows_inv(const __grid_constant__ CUtensorMap gmap, const cf* __restrict__ g0, const cf* __restrict__ g1,
-                   int nx, const cf* __restrict__ nb, const cf* __restrict__ tw, float* __restrict__ f0,
-                   float* __restrict__ f1, int* __restrict__ err) {
-    constexpr int T = L / 16;
-    constexpr int BUF = net::Cfg<L>::BUF;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cf* S = reinterpret_cast<cf*>(smem_raw);
-    cf* E = reinterpret_cast<cf*>(smem_raw + inv_e_offset<L>());
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(E + BUF);
-    const int t = threadIdx.x;
-    const int i = blockIdx.x, comp = blockIdx.y;
-    if (t == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (t == 0) {
-        mbar_expect_tx(bar, (unsigned)(L * sizeof(cf)));
-#pragma unroll 1
-        for (int b = 0; b < L / 2 / kBox; ++b) tma_load_4d(S + 2 * b * kBox, &gmap, 0, i, b * kBox, comp, bar);
-        const cf* g = comp ? g1 : g0;
-        S[L] = ld2(g + (size_t)(L / 2) * nx * kTW + (size_t)i * kTW);  // read back by this thread only
-    }
-    const net::Bases bs = net::load_bases<L>(nb, t);
-    const cf wt = reg::ld_tw(tw, t);
-    const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
-    if (!ok) {
-        // the row never arrived: report, give the copy one more bounded wait, leave
-        if (t == 0) flag_error(err, TDG_ERR_TIMEOUT);
-        mbar_wait(bar, 0);
-        return;
-    }
-    // conj of the Hermitian repack, natural strided: the inverse transform is
-    // conj(fwd(conj(Z)))
-    cf v[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int k = t + T * r;
-        v[r] = conjg(pack_c2r(S[k], S[L - k], reg::twist(wt, r)));
-    }
-    net::fwd<L>(v, E, bs, t);
-    // keep n = perm(t) + T ka < L/2, i.e. ka < 8; transpose back through S
-    const int pt = net::perm<L>(t);
-#pragma unroll
-    for (int ka = 0; ka < 8; ++ka) S[pad(pt + T * ka)] = conjg(v[ka]);
-    __syncthreads();
-    float2* out = reinterpret_cast<float2*>((comp ? f1 : f0) + (size_t)i * L);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const cf o = S[pad(t + T * c)];
-        out[t + T * c] = make_float2(o.x, o.y);
-    }
-}
 
-// Persistent form of pass C: each block walks the (row, component) items b, b + G, ...
-// with the next item's TMA load issued as soon as every thread has repacked the current
-// one, so the load overlaps the transform and the stores.  The cropped output goes
-// through E (the network buffer) instead of S, which by then holds the next row.
+// Persistent: each block walks the (row, component) items b, b + G, ..., issuing the next
+// item's TMA load as soon as every thread has repacked the current one, so that the load
+// overlaps the transform and the stores.  The cropped output goes back through E (the
+// network buffer), since S by then receives the next row.
 template <int L>
 __global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows_inv_p(const __grid_constant__ CUtensorMap gmap, const cf* __restrict__ g0,
+    k_net_rows_inv(const __grid_constant__ CUtensorMap gmap, const cf* __restrict__ g0,
                      const cf* __restrict__ g1, int nx, const cf* __restrict__ nb, const cf* __restrict__ tw,
                      float* __restrict__ f0, float* __restrict__ f1, int* __restrict__ err) {
     constexpr int T = L / 16;
@@ -645,45 +480,44 @@ __global__ void __launch_bounds__(L / 16, 3)
     }
 }
 
+// twiddle factors kept in tensor memory: 32 columns of stage-2 factors at a2, 32 of
+// stage-3 factors at a3 (16 complex values each, in the order the network applies them)
+template <int L>
+struct TmemTw {
+    unsigned a2, a3;
+    // v[i] *= f[i] where the factor is not 1 (i % G != 0)
+    template <int G>
+    __device__ __forceinline__ static void mul16(cf* v, unsigned a) {
+        cf f[16];
+        tmem_load16(a, f);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (i % G) v[i] = cmul(v[i], f[i]);
+    }
+    __device__ __forceinline__ void apply2(cf* v) const { mul16<net::Cfg<L>::R>(v, a2); }
+    __device__ __forceinline__ void apply3(cf* v) const { mul16<16>(v, a3); }
+};
+
 // ---------------------------------------------------------------------------------------
 // pass B: one frequency column ky per block, column length L = nx.
+//
 // Spectra (k_net_spectra): per ky the even half then the odd half, HS = L/2 + 2 entries
 // each, in network order.  The products are conj(i s X) (the inverse transforms run as
 // conj(inv_t(conj(.)))).  For fixed ky, s_x is odd and s_y even in kx, so entries past
 // the middle of a half come from the mirrored entry, with s_x negated.
+//
+// Only the 16 values of the transform in flight live in registers; the rest waits in
+// tensor memory (tcgen05.st / tcgen05.ld, 32 columns a slot, warps w and w + 4 sharing
+// the lane quarter w % 4) or in shared memory:
+//   slot A: the even half's y product, then the even y result;
+//   slot B: the twisted column x_n W_2L^n, then the odd half's y product;
+//   xb (shared): the column (and the solve's transposition), then the even x result;
+//   4096-cell columns: the stage-2 and stage-3 twiddle factors, formed once per block, in
+//   two more slots (256 columns a block, two blocks an SM: the whole tensor memory).
 // ---------------------------------------------------------------------------------------
 template <int L, int H>
-__device__ __forceinline__ void spec_products(cf* wx, cf* v, const float2* __restrict__ sh, int t, int pt,
-                                              int tm) {
-    constexpr int T = L / 16;
-#pragma unroll
-    for (int ka = 0; ka < 16; ++ka) {
-        int idx;
-        bool direct;
-        if (ka < 8) {
-            idx = ka * T + t;
-            direct = true;
-        } else if (H == 0 && pt == 0) {
-            idx = (16 - ka) * T;  // k = T ka, mirror T (16 - ka); ka = 8 is the middle itself
-            direct = ka == 8;
-        } else {
-            idx = (15 - ka) * T + tm;
-            direct = false;
-        }
-        const float2 q = __ldg(sh + idx);
-        const float sx = direct ? q.x : -q.x;
-        const float sy = q.y;
-        const cf x = v[ka];
-        wx[ka] = mk(-sx * x.y, -sx * x.x);
-        v[ka] = mk(-sy * x.y, -sy * x.x);
-    }
-}
-
-// same products; the y product goes to tensor memory at ta in groups of four, and v is
-// left holding the x product
-template <int L, int H>
-__device__ __forceinline__ void spec_products_tm(cf* v, const float2* __restrict__ sh, int t, int pt, int tm,
-                                                 unsigned ta) {
+__device__ __forceinline__ void spec_products(cf* v, const float2* __restrict__ sh, int t, int pt, int tm,
+                                              unsigned ta) {
     constexpr int T = L / 16;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
@@ -697,7 +531,7 @@ __device__ __forceinline__ void spec_products_tm(cf* v, const float2* __restrict
                 idx = ka * T + t;
                 direct = true;
             } else if (H == 0 && pt == 0) {
-                idx = (16 - ka) * T;
+                idx = (16 - ka) * T;  // k = T ka, mirror T (16 - ka); ka = 8 is the middle itself
                 direct = ka == 8;
             } else {
                 idx = (15 - ka) * T + tm;
@@ -707,8 +541,8 @@ __device__ __forceinline__ void spec_products_tm(cf* v, const float2* __restrict
             const float sx = direct ? q.x : -q.x;
             const float sy = q.y;
             const cf x = v[ka];
-            v[ka] = mk(-sx * x.y, -sx * x.x);
-            y[e] = mk(-sy * x.y, -sy * x.x);
+            v[ka] = mk(-sx * x.y, -sx * x.x);  // x product, stays in v
+            y[e] = mk(-sy * x.y, -sy * x.x);   // y product, to tensor memory
         }
         tmem_store4_nowait(ta + 8 * g, y);
     }
@@ -716,50 +550,33 @@ __device__ __forceinline__ void spec_products_tm(cf* v, const float2* __restrict
 }
 
 template <int L>
+constexpr bool cols_twiddles_in_tmem() {
+    return L == 4096;
+}
+
+template <int L>
 constexpr size_t cols_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF + (TDG_COLS_SWAP == 3 ? 0 : 16 * T)) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16;
-}
-
-// blocks per SM pass B is compiled for
-template <int L>
-constexpr int cols_min_blocks() {
-    return (TDG_COLS_SWAP == 3 && L == 4096) ? 3 : 2;
+    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16;
 }
 
 template <int L>
-__global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
+__global__ void __launch_bounds__(L / 16, 2)
     k_net_cols(const cf* __restrict__ z, int solve, const cf* __restrict__ nb, const cf* __restrict__ tw,
                const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     constexpr int HS = L / 2 + 2;
+    constexpr bool kTwt = cols_twiddles_in_tmem<L>();
+    constexpr unsigned kWarpCols = kTwt ? 128 : 64;
+    constexpr unsigned kCols = kTwt ? 256 : (T > 128 ? 128 : 64);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
-    cf* xb = E + BUF;                         // the column (padded natural), later the even y result
-    cf* sb = xb + BUF;                        // the even x result, [r][t] (not with the TMEM stash)
-    cf* edge = sb + (TDG_COLS_SWAP == 3 ? 0 : 16 * T);
+    cf* xb = E + BUF;                         // the column (padded natural), later the even x result
+    cf* edge = xb + BUF;
+    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
     const int t = threadIdx.x;
-#if TDG_COLS_SWAP == 2
-    // 64 TMEM columns: warps w and w + 4 share a lane quarter, 32 columns each
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
-    if (t < 32) tmem_alloc(tslot, 64);
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    const unsigned ta = tmem_thread_addr(*tslot, t);
-#elif TDG_COLS_SWAP == 3
-    // two stash slots of 32 columns per thread: warps w and w + 4 share a lane quarter
-    // (columns 64 (w / 4) + [0, 64)); blocks of at most four warps need 64 columns
-    constexpr unsigned kCols = T > 128 ? 128 : 64;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
     if (t < 32) tmem_alloc(tslot, kCols);
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    const unsigned tA = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + (unsigned)(64 * (t >> 7));
-    const unsigned tB = tA + 32;
-#endif
     const int ky = blockIdx.x;
     const int tile = ky >> 1, c = ky & 1;
     const size_t slab = (size_t)L * kTW;
@@ -772,208 +589,18 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
                      : "memory");
     }
     const net::Bases bs = net::load_bases<L>(nb, t);
-    if (solve) {
-        cf x[16];  // rows 16 t + r, stored at r T + t
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = ld2(zc + (size_t)(r * T + t) * kTW);
-        solve_chunk<cf>(x, t, T, edge);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = x[r];
-        __syncthreads();
-    } else {
-        cf x[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = ld2(zc + (size_t)(t + r * T) * kTW);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = x[r];  // own positions
-    }
-    const int pt = net::perm<L>(t);
-    const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);  // even half: mirror of k is L - k
-    const int to = net::perm_inv<L>(T - 1 - pt);             // odd half: mirror of k is L - 1 - k
-    cf v[16], w[16];
-    // even frequencies X_e = FFT_L(x)
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
-    net::fwd<L>(v, E, bs, t);
-#if TDG_COLS_SWAP == 3
-    // v: X_e -> x product; y product to tensor memory
-    spec_products_tm<L, 0>(v, se, t, pt, te, tA);
-    net::inv_t<L>(v, E, bs, t);
-    tmem_store16(tB, v);  // the even x result stays there until the end
-    tmem_load16(tA, v);
-#else
-    spec_products<L, 0>(w, v, se, t, pt, te);
-#endif
-#if TDG_COLS_SWAP == 3
-#elif TDG_COLS_SWAP == 2
-    tmem_store16(ta, v);  // the y product waits in tensor memory
-    net::inv_t<L>(w, E, bs, t);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) sb[r * T + t] = w[r];
-    tmem_load16(ta, v);
-#elif TDG_COLS_SWAP
-    // the y product waits in sb (this thread's slots) while the x product is transformed
-#pragma unroll
-    for (int r = 0; r < 16; ++r) sb[r * T + t] = v[r];
-    net::inv_t<L>(w, E, bs, t);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        v[r] = sb[r * T + t];
-        sb[r * T + t] = w[r];
-    }
-#else
-    net::inv_t<L>(w, E, bs, t);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) sb[r * T + t] = w[r];
-#endif
-    __syncthreads();
-    net::inv_t<L>(v, E, bs, t);
-    // odd frequencies: X_o = FFT_L(x_n W_2L^n); park the even y result in the column's place
-    {
-        const cf wt = reg::ld_tw(tw, t);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int n = t + r * T;
-            w[r] = cmul(xb[pad(n)], reg::twist(wt, r));
-            xb[pad(n)] = v[r];
-        }
-    }
-    __syncthreads();
-    net::fwd<L>(w, E, bs, t);
-#if TDG_COLS_SWAP == 3
-    spec_products_tm<L, 1>(w, so, t, pt, to, tA);
-#else
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = w[r];
-    spec_products<L, 1>(w, v, so, t, pt, to);
-#endif
-#if TDG_COLS_SWAP == 2
-    tmem_store16(ta, v);
-#endif
-    net::inv_t<L>(w, E, bs, t);
-    // G = conj(u_even + W_2L^n u_odd): W_2L^n as conj of W_2L^-n (table entry 2L - t)
-    const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
-    cf* gxc = gx + (size_t)tile * slab + c;
-    cf* gyc = gy + (size_t)tile * slab + c;
-#if TDG_COLS_SWAP == 3
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        cf ex[4];
-        tmem_load4(tB + 8 * g, ex);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int r = 4 * g + e;
-            const int n = t + r * T;
-            gxc[(size_t)n * kTW] = conjg(ex[e] + cmulc(w[r], reg::untwist(wtc, r)));
-        }
-    }
-    tmem_load16(tA, v);
-#else
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int n = t + r * T;
-        gxc[(size_t)n * kTW] = conjg(sb[r * T + t] + cmulc(w[r], reg::untwist(wtc, r)));
-    }
-#endif
-#if TDG_COLS_SWAP == 2
-    tmem_load16(ta, v);
-#endif
-    __syncthreads();
-    net::inv_t<L>(v, E, bs, t);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int n = t + r * T;
-        gyc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
-    }
-#if TDG_COLS_SWAP == 2
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    if (t < 32) tmem_dealloc(*tslot, 64);
-#elif TDG_COLS_SWAP == 3
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    if (t < 32) tmem_dealloc(*tslot, kCols);
-#endif
-}
-
-// Pass B with its stashes in tensor memory, so that a single 16-value array is live at
-// any time (three blocks of 256 threads per SM).  Per thread two stash slots of 32 TMEM
-// columns (A, B):
-//   x W_2L^n -> B;  X_e = fwd(x);  y product -> A;  inv(x product) -> xb (the column is
-//   dead);  A -> inv(y product) -> A;  B -> X_o = fwd;  y product -> B;
-//   G_x = conj(xb + W^n inv(x product));  B -> G_y = conj(A + W^n inv(y product)).
-#ifndef TDG_COLS_DB
-#define TDG_COLS_DB 0
-#endif
-// 1: for 4096-cell columns the even x result also goes to tensor memory and the column
-// shares the network buffer (one shared buffer per block, the rest left to L1)
-#ifndef TDG_COLS_SLIM
-#define TDG_COLS_SLIM 1
-#endif
-
-template <int L>
-constexpr bool cols_slim() {
-    return TDG_COLS_SLIM && !TDG_COLS_DB && L == 4096;
-}
-
-template <int L>
-constexpr size_t cols_tm_smem_bytes() {
-    constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)((cols_slim<L>() ? 1 : 2 + TDG_COLS_DB) * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16;
-}
-
-#ifndef TDG_COLS_TM_MINB
-#define TDG_COLS_TM_MINB 2
-#endif
-
-template <int L>
-__global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
-    k_net_cols_tm(const cf* __restrict__ z, int solve, const cf* __restrict__ nb, const cf* __restrict__ tw,
-                  const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
-    constexpr int T = L / 16;
-    constexpr int BUF = net::Cfg<L>::BUF;
-    constexpr int HS = L / 2 + 2;
-    constexpr bool kSlim = cols_slim<L>();
-    // warps w and w + 4 share a lane quarter; slots of 32 columns: A, B (and C when slim)
-    constexpr unsigned kCols = kSlim ? 256 : (T > 128 ? 128 : 64);
-    constexpr unsigned kWarpCols = kSlim ? 128 : 64;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
-    // the column (padded natural), later the even x result; slim: the column shares E
-    cf* xb = kSlim ? E : E + BUF;
-    // second network buffer: transforms alternate E, E2 wherever two in a row would
-    // otherwise need a barrier between them (inv_t then inv_t, inv_t then fwd)
-    cf* E2 = TDG_COLS_DB ? xb + BUF : E;
-    cf* edge = kSlim ? E + BUF : xb + (1 + TDG_COLS_DB) * BUF;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
-    const int t = threadIdx.x;
-    if (t < 32) tmem_alloc(tslot, kCols);
-    const int ky = blockIdx.x;
-    const int tile = ky >> 1, c = ky & 1;
-    const size_t slab = (size_t)L * kTW;
-    const cf* zc = z + (size_t)tile * slab + c;
-    const float2* se = spec + (size_t)ky * 2 * HS;
-    const float2* so = se + HS;
-    if (t == 0) {
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(se), "r"((unsigned)(2 * HS * sizeof(float2)))
-                     : "memory");
-    }
-    const net::Bases bs = net::load_bases<L>(nb, t);
     cf v[16];
     if (solve) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = ld2(zc + (size_t)(r * T + t) * kTW);  // rows 16 t + r
-        solve_chunk<cf>(v, t, T, edge);  // its barrier also publishes the TMEM address
+        solve_chunk<cf>(v, t, T, edge);
 #pragma unroll
         for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = v[r];
         tmem_fence_before();
-        __syncthreads();
+        __syncthreads();  // also publishes the tensor-memory address
         tmem_fence_after();
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
-        if (kSlim) __syncthreads();  // the column is read before fwd writes the buffer
     } else {
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = ld2(zc + (size_t)(t + r * T) * kTW);
@@ -983,11 +610,25 @@ __global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
     }
     const unsigned tA = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + kWarpCols * (unsigned)(t >> 7);
     const unsigned tB = tA + 32;
-    const unsigned tC = tA + 64;  // slim only
+    const TmemTw<L> tt{tA + 64, tA + 96};
+    if constexpr (kTwt) {
+        cf f[16], g[16];
+        net::stage_factors<L>(bs, f, g);
+        tmem_store16(tt.a2, f);
+        tmem_store16(tt.a3, g);
+    }
+    auto FWD = [&](cf* vv) {
+        if constexpr (kTwt) net::fwd_p<L>(vv, E, tt, t);
+        else net::fwd<L>(vv, E, bs, t);
+    };
+    auto INV = [&](cf* vv) {
+        if constexpr (kTwt) net::inv_t_p<L>(vv, E, tt, t);
+        else net::inv_t<L>(vv, E, bs, t);
+    };
     const int pt = net::perm<L>(t);
-    const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);
-    const int to = net::perm_inv<L>(T - 1 - pt);
-    // the odd half's input x_n W_2L^n waits in B
+    const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);  // even half: mirror of k is L - k
+    const int to = net::perm_inv<L>(T - 1 - pt);             // odd half: mirror of k is L - 1 - k
+    // the odd half's input x_n W_2L^n waits in slot B
     {
         const cf wt = reg::ld_tw(tw, t);
 #pragma unroll
@@ -999,50 +640,35 @@ __global__ void __launch_bounds__(L / 16, L == 4096 ? TDG_COLS_TM_MINB : 2)
         }
         tmem_wait_st();
     }
-    net::fwd<L>(v, E, bs, t);
-    spec_products_tm<L, 0>(v, se, t, pt, te, tA);
-    net::inv_t<L>(v, E, bs, t);
-    if (kSlim) {
-        tmem_store16(tC, v);
-    } else {
-        // every thread has read its column values from xb before fwd's barrier: reuse it
+    // even frequencies X_e = FFT_L(x)
+    FWD(v);
+    spec_products<L, 0>(v, se, t, pt, te, tA);
+    INV(v);
+    // every thread read its column values from xb before the first barrier of FWD
 #pragma unroll
-        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];  // own slots
-    }
+    for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];  // even x result, own slots
     tmem_load16(tA, v);
-    if (!TDG_COLS_DB) __syncthreads();
-    net::inv_t<L>(v, E2, bs, t);
+    __syncthreads();
+    INV(v);
     tmem_store16(tA, v);  // even y result
     tmem_load16(tB, v);   // x W_2L^n
-    if (!TDG_COLS_DB) __syncthreads();
-    net::fwd<L>(v, E, bs, t);
-    spec_products_tm<L, 1>(v, so, t, pt, to, tB);
-    net::inv_t<L>(v, E, bs, t);
+    __syncthreads();
+    // odd frequencies X_o = FFT_L(x_n W_2L^n)
+    FWD(v);
+    spec_products<L, 1>(v, so, t, pt, to, tB);
+    INV(v);
+    // G = conj(u_even + W_2L^n u_odd); W_2L^n as conj of W_2L^-n (table entry 2L - t)
     const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
     cf* gxc = gx + (size_t)tile * slab + c;
     cf* gyc = gy + (size_t)tile * slab + c;
-    if (kSlim) {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            cf ex[4];
-            tmem_load4(tC + 8 * g, ex);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int r = 4 * g + e;
-                const int n = t + r * T;
-                gxc[(size_t)n * kTW] = conjg(ex[e] + cmulc(v[r], reg::untwist(wtc, r)));
-            }
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int n = t + r * T;
-            gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
-        }
+    for (int r = 0; r < 16; ++r) {
+        const int n = t + r * T;
+        gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
     }
     tmem_load16(tB, v);
-    if (!TDG_COLS_DB) __syncthreads();
-    net::inv_t<L>(v, E2, bs, t);
+    __syncthreads();
+    INV(v);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         cf ey[4];
@@ -1132,54 +758,28 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
     CUtensorMap zmap, gmap;
     if ((e = encode_tiles(&zmap, z, p.nx, ntile, 1, 0))) return e;
     if ((e = encode_tiles(&gmap, gx, p.nx, ntile, 2, n_el * sizeof(cf)))) return e;
-
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
-    size_t sm;
-    if (TDG_ROWS_PERSIST && solve) {
-        sm = rows_p_bytes<LY>();
-        if ((e = set_smem(k_net_rows_p<LY>, sm))) return e;
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_p<LY>, LY / 16, sm))) return e;
-        const int grid = std::min(p.nx, std::max(1, per_sm) * nsm);
-        mark(p, 0, s);
-        k_net_rows_p<LY><<<grid, LY / 16, sm, s>>>(sigma, p.nx, p.nx, bases_y(p), twy, zmap, z);
-    } else {
-        sm = rows_bytes<LY>();
-        if ((e = set_smem(k_net_rows<LY>, sm))) return e;
-        mark(p, 0, s);
-        k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, solve, solve, p.nx, bases_y(p), twy, zmap, z);
-    }
+
+    size_t sm = rows_bytes<LY>();
+    if ((e = set_smem(k_net_rows<LY>, sm))) return e;
+    mark(p, 0, s);
+    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, solve, solve, p.nx, bases_y(p), twy, zmap, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
-#if TDG_COLS_SWAP == 3
-    sm = cols_tm_smem_bytes<LX>();
-    if ((e = set_smem(k_net_cols_tm<LX>, sm))) return e;
-    k_net_cols_tm<LX><<<hy, LX / 16, sm, s>>>(z, solve, bases_x(p), twx,
-                                              reinterpret_cast<const float2*>(p.spec_half), gx, gy);
-#else
     sm = cols_smem_bytes<LX>();
     if ((e = set_smem(k_net_cols<LX>, sm))) return e;
     k_net_cols<LX><<<hy, LX / 16, sm, s>>>(z, solve, bases_x(p), twx, reinterpret_cast<const float2*>(p.spec_half),
                                            gx, gy);
-#endif
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
     sm = inv_bytes<LY>();
-#if TDG_INV_PERSIST
-    if ((e = set_smem(k_net_rows_inv_p<LY>, sm))) return e;
-    {
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv_p<LY>, LY / 16, sm)))
-            return e;
-        const int grid = std::min(2 * p.nx, std::max(1, per_sm) * nsm);
-        k_net_rows_inv_p<LY><<<grid, LY / 16, sm, s>>>(gmap, gx, gy, p.nx, bases_y(p), twy, fx, fy, p.err);
-    }
-#else
     if ((e = set_smem(k_net_rows_inv<LY>, sm))) return e;
-    k_net_rows_inv<LY><<<dim3(p.nx, 2), LY / 16, sm, s>>>(gmap, gx, gy, p.nx, bases_y(p), twy, fx, fy, p.err);
-#endif
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
+    const int grid = std::min(2 * p.nx, std::max(1, per_sm) * nsm);
+    k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, gx, gy, p.nx, bases_y(p), twy, fx, fy, p.err);
     e = cudaGetLastError();
     mark(p, 3, s);
     return e;
@@ -1195,16 +795,16 @@ cudaError_t run_net_x(const Plan& p, const float* sigma, float* fx, float* fy, v
 }
 
 template <int L>
-cudaError_t build_axis(const Plan& p, cf* tab, cudaStream_t s) {
+cudaError_t build_axis(cf* tab, cudaStream_t s) {
     k_net_bases<L><<<(L / 16 + 255) / 256, 256, 0, s>>>(tab);
     return cudaGetLastError();
 }
 
-cudaError_t build_bases(const Plan& p, cf* tab, int n, cudaStream_t s) {
+cudaError_t build_bases(cf* tab, int n, cudaStream_t s) {
     switch (n) {
-        case 1024: return build_axis<1024>(p, tab, s);
-        case 2048: return build_axis<2048>(p, tab, s);
-        default: return build_axis<4096>(p, tab, s);
+        case 1024: return build_axis<1024>(tab, s);
+        case 2048: return build_axis<2048>(tab, s);
+        default: return build_axis<4096>(tab, s);
     }
 }
 
@@ -1227,8 +827,8 @@ size_t net_fp32_table_bytes(const Plan& p) { return (size_t)(p.nx / 8 + p.ny / 8
 cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
     cudaError_t e;
     cf* tab = reinterpret_cast<cf*>(p.net_tw);
-    if ((e = build_bases(p, tab, p.nx, s))) return e;
-    if ((e = build_bases(p, tab + p.nx / 8, p.ny, s))) return e;
+    if ((e = build_bases(tab, p.nx, s))) return e;
+    if ((e = build_bases(tab + p.nx / 8, p.ny, s))) return e;
     switch (p.nx) {
         case 1024: return spectra_axis<1024>(p, s);
         case 2048: return spectra_axis<2048>(p, s);
