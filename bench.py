@@ -140,6 +140,30 @@ class Clocks:
 # algorithmic bytes per pass (FP32: 4-byte reals, 8-byte complex)
 # ------------------------------------------------------------------------------------------
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from the ncu capture summarised in profiles/net_kernels_fp32_4096_full.md
+# (FP32 network path, 4096x4096, order 3).  Valid only for the kernel sources it was taken
+# on: reported when their SHA-256 still matches, null otherwise.
+MEASURED_TRAFFIC = {
+    ("cols_conv", 2, 4096): {"bytes": 268_988_416 + 215_674_880,
+                             "sha256": "320b6ea68e017286089d2e7919d8c13c58dbf8334e593cd54a3adcae58ab906a"},
+}
+TRAFFIC_SOURCES = ("paper_1904_07400_gb300/csrc/net_fp32.cu", "paper_1904_07400_gb300/csrc/fft_net.cuh",
+                   "paper_1904_07400_gb300/csrc/fft_reg.cuh")
+
+
+def measured_traffic(kernel, path, n, form):
+    entry = MEASURED_TRAFFIC.get((kernel, path, n))
+    if entry is None or form != "fp32" or ORDER != 3:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return entry["bytes"] if h.hexdigest() == entry["sha256"] else None
+
+
 def pass_bytes(nx, ny, px, real, path):
     """Compulsory bytes of each pass: every array it must read or write once, spectra as the
     kernel path stores them (generic: both full spectra, P_x reals per frequency column;
@@ -315,7 +339,8 @@ def run_ours(args):
     achieved = algo / (r["per_pass_ms"][dom] * 1e-3) / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
     line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                        "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                        "unit": "GB/s", "frac": round(achieved / peak, 4),
+                        "traffic": measured_traffic(dom, r["path"], n, head),
                         "peak_source": "measured" if pk else "fallback",
                         "algorithmic_bytes": algo,
                         "pass_ms": {k: round(v, 4) for k, v in r["per_pass_ms"].items()},
