@@ -110,6 +110,16 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count,
  * 4).  Errors: INVALID_ARG, UNSUPPORTED (a grid does not fit; the old setting stays). */
 tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref);
 
+/* Second form of the batch (picked by the autotuner): nstreams > 0 runs each grid's own
+ * forward path (the kernels tdg_solve_forces would run for its plan, into the batch's
+ * workspace) on `nstreams` internal streams, grids assigned by decreasing cost to the
+ * least-loaded stream, forked from and joined back to the launch stream with events (so
+ * a launch stays asynchronous and capturable in a CUDA graph).  nstreams = 0 returns to
+ * the persistent kernel.  The paper has no counterpart; this exists because grids on the
+ * FP32 network path solve faster with their own kernels than inside the persistent
+ * generic kernel.  Errors: INVALID_ARG (NULL batch, nstreams outside 0..32), CUDA. */
+tdg_status tdg_batch_set_streams(tdg_batch b, int nstreams);
+
 /* One persistent launch solving every grid of the batch on `stream`: a memset of the
  * dependency counters and one kernel, no host synchronisation.  Work items (row groups,
  * frequency columns, inverse-row groups) are taken in pass order; an item waits for its
@@ -127,7 +137,8 @@ tdg_status tdg_batch_info(const tdg_batch b, int* blocks, int* threads, int* ite
 
 /* Test hook: completions of grid `grid`'s row pass are not counted by later launches
  * (-1 restores normal operation), so its column items exhaust their bounded wait.
- * Exists to test the timeout path without faulting or hanging the device. */
+ * Exists to test the timeout path without faulting or hanging the device; applies to
+ * the persistent kernel only. */
 tdg_status tdg_batch_debug_withhold(tdg_batch b, int grid);
 
 /* Release the batch (synchronises its device). */

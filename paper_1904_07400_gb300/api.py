@@ -129,11 +129,12 @@ class Plan:
 
 
 class Batch:
-    """Many independent FP32 solves in one persistent launch (tdg_batch_*).
+    """Many independent FP32 solves in one call (tdg_batch_*).
 
     The grids' input and output tensors are bound at creation; ``launch()`` solves all of
-    them on the current stream with one kernel and no host synchronisation, so it can be
-    captured in a CUDA graph.
+    them on the current stream with no host synchronisation, so it can be captured in a
+    CUDA graph: by default with one persistent kernel, or (``set_streams(n)``) with each
+    grid's own kernels on n internal streams forked from and joined to the current one.
     """
 
     def __init__(self, plans: list[Plan], sigmas: list[torch.Tensor], outs: list[tuple] | None = None):
@@ -154,7 +155,13 @@ class Batch:
         self.device = plans[0].device
 
     def set_config(self, threads: int, radix_pref: int) -> None:
+        """Persistent-kernel form: threads per block and radix preference."""
+        native.call("tdg_batch_set_streams", self._h, 0)
         native.call("tdg_batch_set_config", self._h, threads, radix_pref)
+
+    def set_streams(self, n: int) -> None:
+        """Streams form: each grid's own kernels on n internal streams (0: persistent)."""
+        native.call("tdg_batch_set_streams", self._h, n)
 
     def info(self) -> dict:
         b, t, i, r = (ctypes.c_int() for _ in range(4))

@@ -1,7 +1,8 @@
-"""Autotuner of the persistent batched launch: tries the kernel's tuning knobs (threads per
-block, radix preference of the transforms) on a batch, times each with CUDA events on the
-current stream, keeps the fastest, and caches the choice in a JSON file keyed by the GPU
-name and the batch's grid signature (sizes, orders, precision)."""
+"""Autotuner of the batched launch: tries the persistent kernel's knobs (threads per block,
+radix preference of the transforms) and the streams form (each grid's own kernels on 2, 4
+8 or 16 internal streams) on a batch, times each with CUDA events on the current stream,
+keeps the fastest, and caches the choice in a JSON file keyed by the GPU name and the
+batch's grid signature (sizes, orders, precision)."""
 from __future__ import annotations
 
 import hashlib
@@ -11,6 +12,7 @@ import os
 import torch
 
 CANDIDATES = [(512, 0), (512, 1), (256, 0), (256, 1)]
+STREAMS = (2, 4, 8, 16)
 
 
 def signature(batch) -> str:
@@ -32,8 +34,15 @@ def _time(batch, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+def _apply(batch, rec: dict) -> None:
+    if rec.get("mode") == "streams":
+        batch.set_streams(rec["streams"])
+    else:
+        batch.set_config(rec["threads"], rec["radix_pref"])
+
+
 def tune(batch, cache_path: str | None = None, reps: int = 5) -> dict:
-    """Pick (threads, radix_pref) for `batch`, apply it, and return the record."""
+    """Pick the batch's form and knobs, apply them, and return the record."""
     key = signature(batch)
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -41,19 +50,25 @@ def tune(batch, cache_path: str | None = None, reps: int = 5) -> dict:
             cache = json.load(f)
     if key in cache:
         rec = cache[key]
-        batch.set_config(rec["threads"], rec["radix_pref"])
+        _apply(batch, rec)
         return rec
-    timings = {}
+    timings, recs = {}, {}
     for threads, radix in CANDIDATES:
+        rec = {"mode": "persistent", "threads": threads, "radix_pref": radix}
         try:
-            batch.set_config(threads, radix)
+            _apply(batch, rec)
         except Exception:
             continue
-        timings[f"{threads}/{radix}"] = _time(batch, reps)
+        name = f"{threads}/{radix}"
+        timings[name], recs[name] = _time(batch, reps), rec
+    for n in STREAMS:
+        rec = {"mode": "streams", "streams": n}
+        _apply(batch, rec)
+        name = f"streams/{n}"
+        timings[name], recs[name] = _time(batch, reps), rec
     best = min(timings, key=timings.get)
-    threads, radix = (int(x) for x in best.split("/"))
-    batch.set_config(threads, radix)
-    rec = {"threads": threads, "radix_pref": radix, "ms": timings[best], "candidates_ms": timings}
+    rec = dict(recs[best], ms=timings[best], candidates_ms=timings)
+    _apply(batch, rec)
     if cache_path:
         cache[key] = rec
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)

@@ -49,10 +49,11 @@ FftPlan make_fft_plan(int L) {
     return fp;
 }
 
-AxisInfo make_axis(int n) {
+// padded period 2M; M = the smallest 2^a 3^b >= n unless a longer M is given
+AxisInfo make_axis(int n, int M = 0) {
     AxisInfo a;
     a.n = n;
-    int M = next_smooth(n);
+    if (M < n) M = next_smooth(n);
     a.P = 2 * M;
     a.half = make_fft_plan(M);
     a.full = make_fft_plan(2 * M);
@@ -219,8 +220,12 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
     p.dy = dy;
     p.G = G;
     p.prec = prec;
-    p.ax = make_axis(nx);
-    p.ay = make_axis(ny);
+    // FP32 grids whose sides are multiples of 16 from 128 to 4096 cells run the transform
+    // network, whose lengths are 512 .. 4096: pad to twice that length (any padded period
+    // of at least 2n - 1 gives the same cropped result)
+    const bool net = prec == TDG_FP32 && net_fp32_length(nx) && net_fp32_length(ny);
+    p.ax = make_axis(nx, net ? net_fp32_length(nx) : 0);
+    p.ay = make_axis(ny, net ? net_fp32_length(ny) : 0);
     p.hy = p.ay.P / 2 + 1;
     p.tw = tile_width(prec);
     p.ntile = (p.hy + p.tw - 1) / p.tw;
@@ -304,15 +309,15 @@ tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
         TDG_TRY(launch_spectra<double>(p, placed_x, placed_y, scratch, reinterpret_cast<double*>(p.spec), s));
     else
         TDG_TRY(launch_spectra<float>(p, placed_x, placed_y, scratch, reinterpret_cast<float*>(p.spec), s));
-    if (fast_fp32_eligible(p)) {
+    if (net_fp32_eligible(p)) {
+        // FP32: one-barrier network kernels, spectra in the network's order
+        TDG_TRY(cudaMalloc(&p.spec_half, net_fp32_spec_bytes(p)));
+        TDG_TRY(cudaMalloc(&p.net_tw, net_fp32_table_bytes(p)));
+        TDG_TRY(launch_net_tables(p, s));
+    } else if (fast_fp32_eligible(p)) {
+        // FP32_TC16: two-exchange register kernels
         TDG_TRY(cudaMalloc(&p.spec_half, fast_fp32_spec_bytes(p)));
-        if (net_fp32_eligible(p)) {
-            // FP32: one-barrier network kernels, spectra in the network's order
-            TDG_TRY(cudaMalloc(&p.net_tw, net_fp32_table_bytes(p)));
-            TDG_TRY(launch_net_tables(p, s));
-        } else {
-            TDG_TRY(launch_half_spectra(p, s));
-        }
+        TDG_TRY(launch_half_spectra(p, s));
     }
     TDG_TRY(cudaStreamSynchronize(s));
     cudaFree(placed_x);

@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -173,6 +174,17 @@ struct tdg_batch_s {
     int* err;
     void* work;
     int withhold;
+    // per-grid pointers (the streams form launches each grid's own forward path)
+    std::vector<const float*> sig;
+    std::vector<float*> fxs, fys;
+    std::vector<void*> wptr;
+    // streams form: 0 = the persistent kernel; n > 0 = grids on n internal streams
+    int nstreams;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork;
+    std::vector<int> lane;  // internal stream of each grid (LPT on the solve cost)
+    std::vector<int> order; // grids by decreasing cost
 };
 
 namespace {
@@ -241,7 +253,21 @@ tdg_status batch_configure(tdg_batch_s* b) {
     return TDG_OK;
 }
 
+void streams_free(tdg_batch_s* b) {
+    for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    b->streams.clear();
+    b->joins.clear();
+    b->fork = nullptr;
+    b->nstreams = 0;
+}
+
+// relative cost of one grid's solve: nx ny log2(P_x P_y)
+double solve_cost(const Plan& p) { return (double)p.nx * p.ny * std::log2((double)p.ax.P * p.ay.P); }
+
 void batch_free(tdg_batch_s* b) {
+    streams_free(b);
     cudaFree(b->disks);
     cudaFree(b->start);
     cudaFree(b->done);
@@ -272,8 +298,14 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
     b->threads = 512;
     b->radix_pref = 0;
     b->withhold = -1;
+    b->nstreams = 0;
+    b->fork = nullptr;
     b->plans.assign(plans, plans + count);
     b->host.resize(count);
+    b->sig.resize(count);
+    b->fxs.resize(count);
+    b->fys.resize(count);
+    b->wptr.resize(count);
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
@@ -302,6 +334,10 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
         g.sigma = (const float*)sigma[d];
         g.fx = (float*)fx[d];
         g.fy = (float*)fy[d];
+        b->sig[d] = g.sigma;
+        b->fxs[d] = g.fx;
+        b->fys[d] = g.fy;
+        b->wptr[d] = (char*)b->work + off[d];
         g.tiled.tw = RowCfg<float>::TW;
         g.tiled.slab = (size_t)p.nx * g.tiled.tw;
         const size_t n_el = (size_t)p.ntile * g.tiled.slab;
@@ -346,12 +382,69 @@ tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref) {
     return st;
 }
 
+tdg_status tdg_batch_set_streams(tdg_batch b, int nstreams) {
+    if (!b || nstreams < 0 || nstreams > 32) return TDG_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    streams_free(b);
+    cudaError_t e = cudaSuccess;
+    if (nstreams > 0) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int k = 0; k < nstreams && e == cudaSuccess; ++k) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) b->streams.push_back(st);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->joins.push_back(ev);
+        }
+        if (e == cudaSuccess) {
+            // grids by decreasing cost, each to the least-loaded stream
+            std::vector<double> cost(b->count), load(nstreams, 0.0);
+            b->order.resize(b->count);
+            b->lane.assign(b->count, 0);
+            for (int d = 0; d < b->count; ++d) {
+                cost[d] = solve_cost(tdg_plan_internal(b->plans[d]));
+                b->order[d] = d;
+            }
+            std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+            for (int d : b->order) {
+                const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                b->lane[d] = k;
+                load[k] += cost[d];
+            }
+            b->nstreams = nstreams;
+        } else {
+            streams_free(b);
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return e == cudaSuccess ? TDG_OK : TDG_ERR_CUDA;
+}
+
 tdg_status tdg_batch_launch(tdg_batch b, tdg_stream stream) {
     if (!b) return TDG_ERR_INVALID_ARG;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (b->nstreams > 0) {
+        // fork onto the internal streams, each grid's own forward path, join back
+        cudaError_t e = cudaEventRecord(b->fork, s);
+        for (int k = 0; k < b->nstreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
+        for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+            const int d = b->order[i];
+            e = launch_forward<float>(tdg_plan_internal(b->plans[d]), b->sig[d], b->fxs[d], b->fys[d], b->wptr[d],
+                                      b->streams[b->lane[d]]);
+        }
+        for (int k = 0; k < b->nstreams && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(b->joins[k], b->streams[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joins[k], 0);
+        }
+        if (prev >= 0) cudaSetDevice(prev);
+        return e == cudaSuccess ? TDG_OK : TDG_ERR_CUDA;
+    }
     cudaError_t e = cudaMemsetAsync(b->done, 0, (kPhases * b->count + 1) * sizeof(int), s);
     if (e == cudaSuccess) {
         BatchDev dv;

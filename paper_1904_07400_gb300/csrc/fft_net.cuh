@@ -1,4 +1,4 @@
-// Register FFT network of length L = 16 * R * 16 (R in {4, 8, 16}) run by T = L / 16
+// Register FFT network of length L = 16 * R * 16 (R in {2, 4, 8, 16}) run by T = L / 16
 // threads with 16 complex values each, with ONE block barrier per transform.
 //
 // Index decomposition: n = a + 16 b + 16 R c and k = k_c + 16 k_b + 16 R k_a
@@ -41,7 +41,7 @@ struct Cfg {
     static constexpr int NM = 16 / R;  // stage-2 groups per thread
     static constexpr int SLAB = 272;
     static constexpr int BUF = R * SLAB;  // complex values per exchange buffer
-    static_assert(R == 4 || R == 8 || R == 16, "L in {1024, 2048, 4096}");
+    static_assert(R == 2 || R == 4 || R == 8 || R == 16, "L in {512, 1024, 2048, 4096}");
 };
 
 template <int L>
@@ -86,9 +86,14 @@ __device__ __forceinline__ void tw2(cf* v, cf b2) {
         const cf w1b = reg::mul_w16(b2, 1);
         reg::apply_powers<8>(v, b2, csq(csq(b2)), b2);
         reg::apply_powers<8>(v + 8, w1b, csq(csq(w1b)), w1b);
-    } else {
+    } else if constexpr (R == 4) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) reg::apply_powers<4>(v + 4 * m, reg::mul_w16(b2, m), b2, b2);
+    } else {
+        // R = 2: W_32^(j + 2 m) = W_32^j W_16^m, one factor per pair
+#pragma unroll
+        for (int m = 1; m < 8; ++m) v[2 * m + 1] = cmul(v[2 * m + 1], reg::mul_w16(b2, m));
+        v[1] = cmul(v[1], b2);
     }
 }
 

@@ -227,6 +227,9 @@ __device__ __forceinline__ void butterflies(cf* v, cf* ws = nullptr, const TcCon
     } else if constexpr (R == 8) {
         dft8<1>(v);
         dft8<1>(v + 8);
+    } else if constexpr (R == 2) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) dft2(v[2 * m], v[2 * m + 1]);
     } else {
         dft4(v[0], v[1], v[2], v[3]);
         dft4(v[4], v[5], v[6], v[7]);

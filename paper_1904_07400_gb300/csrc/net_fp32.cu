@@ -101,10 +101,11 @@ __device__ __forceinline__ cf shfl_down1(cf a) {
     return mk(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
 }
 
-// x: the thread's chunk (in: s, out: c).  edge: 2 * (nthreads / 32) values of shared
-// memory.  Called by every thread of the block (one __syncthreads).
+// x: the thread's chunk (in: s, out: c).  The line has 16 nact values (threads t < nact
+// own them; the others hold zeros and get zeros back).  edge: 2 * (nthreads / 32) values
+// of shared memory.  Called by all nthreads threads of the block (one __syncthreads).
 template <typename V>
-__device__ __forceinline__ void solve_chunk(V* x, int t, int nthreads, V* edge) {
+__device__ __forceinline__ void solve_chunk(V* x, int t, int nact, int nthreads, V* edge) {
     constexpr SolveTabs K = make_solve_tabs();
     const float li = (float)kLamInf;
     // forward sweep from zero (exact start on the first chunk)
@@ -133,9 +134,10 @@ __device__ __forceinline__ void solve_chunk(V* x, int t, int nthreads, V* edge) 
     if (lane == 0) yprev = w > 0 ? edge[w - 1] : vzero(ylast);
     if (lane == 31) cnext = w + 1 < nw ? edge[nw + w + 1] : vzero(ylast);
     const V Y = t > 0 ? yprev : vzero(ylast);
-    const V C = t + 1 < nthreads ? vfma(ylast, K.h[0], cnext) : vzero(ylast);
+    const V C = t + 1 < nact ? vfma(ylast, K.h[0], cnext) : vzero(ylast);
+    const float keep = t < nact ? 1.0f : 0.0f;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) x[r] = vfma(C, K.g[r], vfma(Y, K.h[r], x[r]));
+    for (int r = 0; r < 16; ++r) x[r] = vs(vfma(C, K.g[r], vfma(Y, K.h[r], x[r])), keep);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -325,7 +327,7 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // ---------------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows(const float* __restrict__ sigma, int solve, int rowmap, int nx, const cf* __restrict__ nb,
+    k_net_rows(const float* __restrict__ sigma, int ny, int solve, int rowmap, int nx, const cf* __restrict__ nb,
                const cf* __restrict__ tw, const __grid_constant__ CUtensorMap zmap, cf* __restrict__ z) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
@@ -337,19 +339,20 @@ __global__ void __launch_bounds__(L / 16, 3)
     const int i = blockIdx.x;
     const net::Bases bs = net::load_bases<L>(nb, t);
     cf v[16];
+    const int nact = ny >> 4;  // threads owning a 16-value chunk of the row
     if (solve) {
-        // thread t owns s[16 t .. 16 t + 15]
-        const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * L) + 4 * t;
+        // thread t owns s[16 t .. 16 t + 15]; past the row: zeros
+        const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * ny) + 4 * t;
         float x[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float4 f = src[q];
+            const float4 f = t < nact ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
             x[4 * q] = f.x;
             x[4 * q + 1] = f.y;
             x[4 * q + 2] = f.z;
             x[4 * q + 3] = f.w;
         }
-        solve_chunk<float>(x, t, T, edge);
+        solve_chunk<float>(x, t, nact, T, edge);
         // chunk -> natural-strided pairs through U (float index f at f + 4 (f / 32))
         float* uf = reinterpret_cast<float*>(U);
 #pragma unroll
@@ -364,10 +367,10 @@ __global__ void __launch_bounds__(L / 16, 3)
             v[c] = mk(p.x, p.y);
         }
     } else {
-        const float2* row = reinterpret_cast<const float2*>(sigma + (size_t)i * L);
+        const float2* row = reinterpret_cast<const float2*>(sigma + (size_t)i * ny);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const float2 p = row[t + T * c];
+            const float2 p = 2 * (t + T * c) < ny ? row[t + T * c] : make_float2(0.f, 0.f);
             v[c] = mk(p.x, p.y);
         }
     }
@@ -423,7 +426,7 @@ constexpr int inv_e_offset() {
 template <int L>
 __global__ void __launch_bounds__(L / 16, 3)
     k_net_rows_inv(const __grid_constant__ CUtensorMap gmap, const cf* __restrict__ g0,
-                     const cf* __restrict__ g1, int nx, const cf* __restrict__ nb, const cf* __restrict__ tw,
+                     const cf* __restrict__ g1, int nx, int ny, const cf* __restrict__ nb, const cf* __restrict__ tw,
                      float* __restrict__ f0, float* __restrict__ f1, int* __restrict__ err) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
@@ -471,11 +474,12 @@ __global__ void __launch_bounds__(L / 16, 3)
 #pragma unroll
         for (int ka = 0; ka < 8; ++ka) E[pad(pt + T * ka)] = conjg(v[ka]);
         __syncthreads();
-        float2* out = reinterpret_cast<float2*>((comp ? f1 : f0) + (size_t)i * L);
+        float2* out = reinterpret_cast<float2*>((comp ? f1 : f0) + (size_t)i * ny);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const cf o = E[pad(t + T * c)];
-            out[t + T * c] = make_float2(o.x, o.y);
+            const int n = t + T * c;
+            const cf o = E[pad(n)];
+            if (2 * n < ny) out[n] = make_float2(o.x, o.y);  // crop to the grid
         }
     }
 }
@@ -515,9 +519,56 @@ struct TmemTw {
 //   4096-cell columns: the stage-2 and stage-3 twiddle factors, formed once per block, in
 //   two more slots (256 columns a block, two blocks an SM: the whole tensor memory).
 // ---------------------------------------------------------------------------------------
+// Per-thread stash of 16 complex values: tensor memory (32 columns of the thread's lane)
+// for columns of 1024 cells and more; shared memory ([r][t], the thread's own slots) for
+// 512, whose one-warp blocks would need more tensor memory per SM than there is.
+template <int L>
+struct Stash {
+    static constexpr bool kTmem = L >= 1024;
+    unsigned ta;  // tensor memory address of the slot (kTmem)
+    cf* sa;       // shared slot base (!kTmem): element r of thread t at sa[r T + t]
+    int t;
+    __device__ __forceinline__ void store16(const cf* v) const {
+        if constexpr (kTmem) {
+            tmem_store16(ta, v);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) sa[r * (L / 16) + t] = v[r];
+        }
+    }
+    __device__ __forceinline__ void load16(cf* v) const {
+        if constexpr (kTmem) {
+            tmem_load16(ta, v);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = sa[r * (L / 16) + t];
+        }
+    }
+    // group g of four values (r = 4 g .. 4 g + 3); stores complete at store_done()
+    __device__ __forceinline__ void store4(int g, const cf* v) const {
+        if constexpr (kTmem) {
+            tmem_store4_nowait(ta + 8 * g, v);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sa[(4 * g + e) * (L / 16) + t] = v[e];
+        }
+    }
+    __device__ __forceinline__ void store_done() const {
+        if constexpr (kTmem) tmem_wait_st();
+    }
+    __device__ __forceinline__ void load4(int g, cf* v) const {
+        if constexpr (kTmem) {
+            tmem_load4(ta + 8 * g, v);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = sa[(4 * g + e) * (L / 16) + t];
+        }
+    }
+};
+
 template <int L, int H>
 __device__ __forceinline__ void spec_products(cf* v, const float2* __restrict__ sh, int t, int pt, int tm,
-                                              unsigned ta) {
+                                              const Stash<L>& ys) {
     constexpr int T = L / 16;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
@@ -542,11 +593,11 @@ __device__ __forceinline__ void spec_products(cf* v, const float2* __restrict__ 
             const float sy = q.y;
             const cf x = v[ka];
             v[ka] = mk(-sx * x.y, -sx * x.x);  // x product, stays in v
-            y[e] = mk(-sy * x.y, -sy * x.x);   // y product, to tensor memory
+            y[e] = mk(-sy * x.y, -sy * x.x);   // y product, to the stash
         }
-        tmem_store4_nowait(ta + 8 * g, y);
+        ys.store4(g, y);
     }
-    tmem_wait_st();
+    ys.store_done();
 }
 
 template <int L>
@@ -557,16 +608,19 @@ constexpr bool cols_twiddles_in_tmem() {
 template <int L>
 constexpr size_t cols_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16;
+    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16 +
+           (Stash<L>::kTmem ? 0 : (size_t)2 * 16 * T * sizeof(cf));
 }
 
+// column length nx <= L (a multiple of 16); Z, G_x, G_y hold nx rows
 template <int L>
 __global__ void __launch_bounds__(L / 16, 2)
-    k_net_cols(const cf* __restrict__ z, int solve, const cf* __restrict__ nb, const cf* __restrict__ tw,
+    k_net_cols(const cf* __restrict__ z, int nx, int solve, const cf* __restrict__ nb, const cf* __restrict__ tw,
                const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     constexpr int HS = L / 2 + 2;
+    constexpr bool kTm = Stash<L>::kTmem;
     constexpr bool kTwt = cols_twiddles_in_tmem<L>();
     constexpr unsigned kWarpCols = kTwt ? 128 : 64;
     constexpr unsigned kCols = kTwt ? 256 : (T > 128 ? 128 : 64);
@@ -575,11 +629,14 @@ __global__ void __launch_bounds__(L / 16, 2)
     cf* xb = E + BUF;                         // the column (padded natural), later the even x result
     cf* edge = xb + BUF;
     unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
+    cf* sslots = reinterpret_cast<cf*>(tslot + 4);  // shared stash slots A, B (L = 512)
     const int t = threadIdx.x;
-    if (t < 32) tmem_alloc(tslot, kCols);
+    if constexpr (kTm) {
+        if (t < 32) tmem_alloc(tslot, kCols);
+    }
     const int ky = blockIdx.x;
     const int tile = ky >> 1, c = ky & 1;
-    const size_t slab = (size_t)L * kTW;
+    const size_t slab = (size_t)nx * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
     const float2* se = spec + (size_t)ky * 2 * HS;
     const float2* so = se + HS;
@@ -589,11 +646,13 @@ __global__ void __launch_bounds__(L / 16, 2)
                      : "memory");
     }
     const net::Bases bs = net::load_bases<L>(nb, t);
+    const int nact = nx >> 4;
     cf v[16];
     if (solve) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = ld2(zc + (size_t)(r * T + t) * kTW);  // rows 16 t + r
-        solve_chunk<cf>(v, t, T, edge);
+        for (int r = 0; r < 16; ++r)  // row 16 t + r sits at r (nx / 16) + t
+            v[r] = t < nact ? ld2(zc + (size_t)(r * nact + t) * kTW) : mk(0.f, 0.f);
+        solve_chunk<cf>(v, t, nact, T, edge);
 #pragma unroll
         for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = v[r];
         tmem_fence_before();
@@ -603,13 +662,17 @@ __global__ void __launch_bounds__(L / 16, 2)
         for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
     } else {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = ld2(zc + (size_t)(t + r * T) * kTW);
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            v[r] = n < nx ? ld2(zc + (size_t)n * kTW) : mk(0.f, 0.f);
+        }
         tmem_fence_before();
         __syncthreads();
         tmem_fence_after();
     }
-    const unsigned tA = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + kWarpCols * (unsigned)(t >> 7);
-    const unsigned tB = tA + 32;
+    const unsigned tA = kTm ? *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + kWarpCols * (unsigned)(t >> 7) : 0u;
+    const Stash<L> sA{tA, sslots, t};
+    const Stash<L> sB{tA + 32, sslots + 16 * T, t};
     const TmemTw<L> tt{tA + 64, tA + 96};
     if constexpr (kTwt) {
         cf f[16], g[16];
@@ -636,54 +699,57 @@ __global__ void __launch_bounds__(L / 16, 2)
             cf y[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) y[e] = cmul(v[4 * g + e], reg::twist(wt, 4 * g + e));
-            tmem_store4_nowait(tB + 8 * g, y);
+            sB.store4(g, y);
         }
-        tmem_wait_st();
+        sB.store_done();
     }
     // even frequencies X_e = FFT_L(x)
     FWD(v);
-    spec_products<L, 0>(v, se, t, pt, te, tA);
+    spec_products<L, 0>(v, se, t, pt, te, sA);
     INV(v);
     // every thread read its column values from xb before the first barrier of FWD
 #pragma unroll
     for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];  // even x result, own slots
-    tmem_load16(tA, v);
+    sA.load16(v);
     __syncthreads();
     INV(v);
-    tmem_store16(tA, v);  // even y result
-    tmem_load16(tB, v);   // x W_2L^n
+    sA.store16(v);  // even y result
+    sB.load16(v);   // x W_2L^n
     __syncthreads();
     // odd frequencies X_o = FFT_L(x_n W_2L^n)
     FWD(v);
-    spec_products<L, 1>(v, so, t, pt, to, tB);
+    spec_products<L, 1>(v, so, t, pt, to, sB);
     INV(v);
-    // G = conj(u_even + W_2L^n u_odd); W_2L^n as conj of W_2L^-n (table entry 2L - t)
+    // G = conj(u_even + W_2L^n u_odd); W_2L^n as conj of W_2L^-n (table entry 2L - t);
+    // rows past the grid are not stored
     const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
     cf* gxc = gx + (size_t)tile * slab + c;
     cf* gyc = gy + (size_t)tile * slab + c;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int n = t + r * T;
-        gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+        if (n < nx) gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
     }
-    tmem_load16(tB, v);
+    sB.load16(v);
     __syncthreads();
     INV(v);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         cf ey[4];
-        tmem_load4(tA + 8 * g, ey);
+        sA.load4(g, ey);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int r = 4 * g + e;
             const int n = t + r * T;
-            gyc[(size_t)n * kTW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
+            if (n < nx) gyc[(size_t)n * kTW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
         }
     }
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    if (t < 32) tmem_dealloc(*tslot, kCols);
+    if constexpr (kTm) {
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (t < 32) tmem_dealloc(*tslot, kCols);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -739,9 +805,12 @@ size_t inv_bytes() {
     return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16;
 }
 
-// bases tables of the plan: x axis first (2 T_x values), then y (2 T_y)
+// transform length of an axis (P / 2) and the plan's bases tables: x axis first (2 T_x
+// values), then y (2 T_y)
+int len_x(const Plan& p) { return p.ax.P / 2; }
+int len_y(const Plan& p) { return p.ay.P / 2; }
 const cf* bases_x(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw); }
-const cf* bases_y(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw) + p.nx / 8; }
+const cf* bases_y(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw) + len_x(p) / 8; }
 
 template <int LX, int LY>
 cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
@@ -765,13 +834,13 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
     size_t sm = rows_bytes<LY>();
     if ((e = set_smem(k_net_rows<LY>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, solve, solve, p.nx, bases_y(p), twy, zmap, z);
+    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, solve, solve, p.nx, bases_y(p), twy, zmap, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_smem_bytes<LX>();
     if ((e = set_smem(k_net_cols<LX>, sm))) return e;
-    k_net_cols<LX><<<hy, LX / 16, sm, s>>>(z, solve, bases_x(p), twx, reinterpret_cast<const float2*>(p.spec_half),
-                                           gx, gy);
+    k_net_cols<LX><<<hy, LX / 16, sm, s>>>(z, p.nx, solve, bases_x(p), twx,
+                                           reinterpret_cast<const float2*>(p.spec_half), gx, gy);
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
     sm = inv_bytes<LY>();
@@ -779,7 +848,7 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
     const int grid = std::min(2 * p.nx, std::max(1, per_sm) * nsm);
-    k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, gx, gy, p.nx, bases_y(p), twy, fx, fy, p.err);
+    k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, gx, gy, p.nx, p.ny, bases_y(p), twy, fx, fy, p.err);
     e = cudaGetLastError();
     mark(p, 3, s);
     return e;
@@ -787,7 +856,8 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
 
 template <int LX>
 cudaError_t run_net_x(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
-    switch (p.ny) {
+    switch (len_y(p)) {
+        case 512: return run_net<LX, 512>(p, sigma, fx, fy, work, s);
         case 1024: return run_net<LX, 1024>(p, sigma, fx, fy, work, s);
         case 2048: return run_net<LX, 2048>(p, sigma, fx, fy, work, s);
         default: return run_net<LX, 4096>(p, sigma, fx, fy, work, s);
@@ -802,6 +872,7 @@ cudaError_t build_axis(cf* tab, cudaStream_t s) {
 
 cudaError_t build_bases(cf* tab, int n, cudaStream_t s) {
     switch (n) {
+        case 512: return build_axis<512>(tab, s);
         case 1024: return build_axis<1024>(tab, s);
         case 2048: return build_axis<2048>(tab, s);
         default: return build_axis<4096>(tab, s);
@@ -818,18 +889,29 @@ cudaError_t spectra_axis(const Plan& p, cudaStream_t s) {
 
 }  // namespace
 
-bool net_fp32_eligible(const Plan& p) {
-    return p.prec == TDG_FP32 && fast_fp32_eligible(p) && encode_fn() != nullptr;
+int net_fp32_length(int n) {
+    if (n < 128 || n > 4096 || n % 16 != 0) return 0;
+    int L = 512;
+    while (L < n) L *= 2;
+    return L;
 }
 
-size_t net_fp32_table_bytes(const Plan& p) { return (size_t)(p.nx / 8 + p.ny / 8) * sizeof(cf); }
+bool net_fp32_eligible(const Plan& p) {
+    return p.prec == TDG_FP32 && net_fp32_length(p.nx) == len_x(p) && net_fp32_length(p.ny) == len_y(p) &&
+           encode_fn() != nullptr;
+}
+
+size_t net_fp32_table_bytes(const Plan& p) { return (size_t)(len_x(p) / 8 + len_y(p) / 8) * sizeof(cf); }
+
+size_t net_fp32_spec_bytes(const Plan& p) { return (size_t)p.hy * 2 * (len_x(p) / 2 + 2) * sizeof(float2); }
 
 cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
     cudaError_t e;
     cf* tab = reinterpret_cast<cf*>(p.net_tw);
-    if ((e = build_bases(tab, p.nx, s))) return e;
-    if ((e = build_bases(tab + p.nx / 8, p.ny, s))) return e;
-    switch (p.nx) {
+    if ((e = build_bases(tab, len_x(p), s))) return e;
+    if ((e = build_bases(tab + len_x(p) / 8, len_y(p), s))) return e;
+    switch (len_x(p)) {
+        case 512: return spectra_axis<512>(p, s);
         case 1024: return spectra_axis<1024>(p, s);
         case 2048: return spectra_axis<2048>(p, s);
         default: return spectra_axis<4096>(p, s);
@@ -838,7 +920,8 @@ cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
 
 cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                cudaStream_t s) {
-    switch (p.nx) {
+    switch (len_x(p)) {
+        case 512: return run_net_x<512>(p, sigma, fx, fy, work, s);
         case 1024: return run_net_x<1024>(p, sigma, fx, fy, work, s);
         case 2048: return run_net_x<2048>(p, sigma, fx, fy, work, s);
         default: return run_net_x<4096>(p, sigma, fx, fy, work, s);

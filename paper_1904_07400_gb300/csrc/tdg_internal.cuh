@@ -112,8 +112,10 @@ size_t fast_fp32_spec_bytes(const Plan& p);
 cudaError_t launch_half_spectra(const Plan& p, cudaStream_t s);
 cudaError_t launch_forward_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                 cudaStream_t s);
+int net_fp32_length(int n);  // FP32 network transform length for a side of n cells, 0: none
 bool net_fp32_eligible(const Plan& p);
 size_t net_fp32_table_bytes(const Plan& p);
+size_t net_fp32_spec_bytes(const Plan& p);
 cudaError_t launch_net_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                cudaStream_t s);

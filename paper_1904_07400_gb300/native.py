@@ -33,6 +33,7 @@ SIGNATURES = [
     ("tdg_batch_create", _c_int, [ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), _c_int,
                                   ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p)]),
     ("tdg_batch_set_config", _c_int, [_c_void_p, _c_int, _c_int]),
+    ("tdg_batch_set_streams", _c_int, [_c_void_p, _c_int]),
     ("tdg_batch_launch", _c_int, [_c_void_p, _c_void_p]),
     ("tdg_batch_get_error", _c_int, [_c_void_p]),
     ("tdg_batch_info", _c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),

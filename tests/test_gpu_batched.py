@@ -136,9 +136,14 @@ def test_autotuner_picks_and_caches(grids, tmp_path):
     b = Batch(plans, sig)
     path = tmp_path / "tune.json"
     rec = autotune.tune(b, str(path), reps=2)
-    assert path.exists() and rec["threads"] in (256, 512)
+    assert path.exists() and rec["mode"] in ("persistent", "streams")
+    assert set(rec["candidates_ms"]) >= {"512/0", "streams/4"}
+    if rec["mode"] == "persistent":
+        assert rec["threads"] in (256, 512)
+    else:
+        assert rec["streams"] in autotune.STREAMS
     rec2 = autotune.tune(b, str(path))
-    assert rec2["threads"] == rec["threads"] and rec2["radix_pref"] == rec["radix_pref"]
+    assert {k: rec2[k] for k in rec2 if k != "candidates_ms"} == {k: rec[k] for k in rec if k != "candidates_ms"}
     b.launch()
     torch.cuda.synchronize()
     _check(b.outs, ref)
@@ -151,3 +156,46 @@ def test_solve_forces_batched_convenience(grids):
     outs = forces_batched(plans, sig)
     torch.cuda.synchronize()
     _check(outs, ref)
+
+
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_streams_form_matches_and_switches_back(grids, n):
+    import torch
+    from paper_1904_07400_gb300.api import Batch
+    plans, sig, ref = grids
+    b = Batch(plans, sig)
+    b.set_streams(n)
+    b.launch()
+    torch.cuda.synchronize()
+    _check(b.outs, ref)
+    for o in b.outs:
+        o[0].zero_()
+        o[1].zero_()
+    b.set_config(512, 0)  # back to the persistent kernel
+    b.launch()
+    torch.cuda.synchronize()
+    assert b.error() == 0
+    _check(b.outs, ref)
+
+
+def test_streams_form_graph_capture_and_replay(grids):
+    import torch
+    from paper_1904_07400_gb300.api import Batch
+    plans, sig, ref = grids
+    b = Batch(plans, sig)
+    b.set_streams(4)
+    b.launch()  # first launch outside the capture (kernel attributes, workspaces)
+    torch.cuda.synchronize()
+    for o in b.outs:
+        o[0].zero_()
+        o[1].zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.launch()
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    _check(b.outs, ref)

@@ -82,3 +82,29 @@ def test_tc16_form_vs_oracle():
     rx, ry = oracle_solver(nx, ny, 3, dx, dy).forces(sigma)
     tc = _forces(nx, ny, 3, dx, dy, "fp32_tc16", sigma)
     assert rel_l2_pair(*tc, rx, ry) <= TOL_FP32
+
+
+# sides that are multiples of 16 below the transform length (the plan pads to P = 2L,
+# L in {512, 1024, 2048, 4096}; the crop is exact for any P >= 2N - 1)
+@pytest.mark.parametrize("shape,k", [((768, 1024), 3), ((1024, 768), 2), ((512, 384), 1), ((384, 512), 3),
+                                     ((128, 160), 3), ((1040, 272), 2), ((3072, 4096), 3), ((144, 2000), 1)])
+def test_padded_network_sizes_vs_fp64_gpu(shape, k):
+    nx, ny = shape
+    dx, dy = 1.0 / nx, 1.0 / ny
+    sigma = syn.clumps(nx, ny, seed=nx + ny + k)
+    f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
+    f64 = _forces(nx, ny, k, dx, dy, "fp64", sigma)
+    assert rel_l2_pair(*f32, *f64) <= TOL_FP32
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_padded_network_small_grid_vs_oracle(k):
+    from paper_1904_07400_gb300.api import Plan
+    nx, ny = 176, 144
+    dx, dy = 1.0 / nx, 0.8 / ny
+    assert Plan(nx, ny, k, dx, dy, precision="fp32").path() == 2
+    rng = np.random.default_rng(k)
+    sigma = rng.random((nx, ny))  # touches every edge
+    rx, ry = oracle_solver(nx, ny, k, dx, dy).forces(sigma)
+    f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
+    assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
