@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--forms", default="fp32,fp32_tc16,fp64")
     ap.add_argument("--size", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-depth", type=int, default=3,
+                    help="end-to-end steps in flight (one stream and workspace each)")
     ap.add_argument("--batched", action="store_true",
                     help="time the uneven batch (256 grids, one persistent launch) instead")
     return ap.parse_args()
@@ -226,11 +228,11 @@ def time_form(form, sigma_host, n, K, W, world, rank, clocks=None):
 
     # end to end through the public API: every step copies its input from pinned host
     # memory, solves, and copies both components back to pinned host memory.  Consecutive
-    # steps alternate between two streams, each with its own device buffers and plan
-    # workspace, so one step's copies overlap the next step's solve (the copy engines
+    # steps rotate over E2E_DEPTH streams, each with its own device buffers and plan
+    # workspace, so one step's copies overlap the next steps' solves (the copy engines
     # and the SMs work at the same time).
     h_sig = torch.as_tensor(sigma_host, dtype=plan.dtype).pin_memory()
-    depth = 2
+    depth = max(1, E2E_DEPTH)
     lanes = []
     for _ in range(depth):
         lanes.append({
@@ -516,8 +518,13 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+E2E_DEPTH = 3
+
+
 def main():
+    global E2E_DEPTH
     args = parse()
+    E2E_DEPTH = args.e2e_depth
     if args.batched:
         run_batched(args)
         return

@@ -1,6 +1,6 @@
 """Autotuner of the batched launch: tries the persistent kernel's knobs (threads per block,
-radix preference of the transforms) and the streams form (each grid's own kernels on 2, 4
-8 or 16 internal streams) on a batch, times each with CUDA events on the current stream,
+radix preference of the transforms) and the streams form (each grid's own kernels on 2,
+4, 8 or 16 internal streams) on a batch, times each with CUDA events on the current stream,
 keeps the fastest, and caches the choice in a JSON file keyed by the GPU name and the
 batch's grid signature (sizes, orders, precision)."""
 from __future__ import annotations

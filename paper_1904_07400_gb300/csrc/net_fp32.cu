@@ -1,4 +1,5 @@
-// FP32 force solve for grids whose sides are 1024, 2048 or 4096 cells, built around the
+// FP32 force solve (and its adjoint) for grids whose sides are multiples of 16 from 128 to
+// 4096 cells, padded to transform lengths L in {512, 1024, 2048, 4096}, built around the
 // one-barrier register FFT network of fft_net.cuh and the data movement of sm_103a:
 //
 //  * pass A (rows): chunked register spline solve, packed real transform, unpack, and a
@@ -522,9 +523,9 @@ struct TmemTw {
 // Per-thread stash of 16 complex values: tensor memory (32 columns of the thread's lane)
 // for columns of 1024 cells and more; shared memory ([r][t], the thread's own slots) for
 // 512, whose one-warp blocks would need more tensor memory per SM than there is.
-template <int L>
+template <int L, bool TM = (L >= 1024)>
 struct Stash {
-    static constexpr bool kTmem = L >= 1024;
+    static constexpr bool kTmem = TM;
     unsigned ta;  // tensor memory address of the slot (kTmem)
     cf* sa;       // shared slot base (!kTmem): element r of thread t at sa[r T + t]
     int t;
@@ -753,6 +754,286 @@ __global__ void __launch_bounds__(L / 16, 2)
 }
 
 // ---------------------------------------------------------------------------------------
+// The adjoint (dL/dsigma for L = sum g_x F^x + g_y F^y): the same passes transposed.
+// w^x and w^y are odd in their force direction, so the transpose of each convolution is
+// its negation: dL/dC = -(K_x g_x + K_y g_y) on the grid, then the spline solves (T is
+// symmetric).  Pass A runs k_net_rows on g_x and g_y (no solve, natural row order).
+// ---------------------------------------------------------------------------------------
+// conj(-i s X) = i s conj(X) = (s X.y, s X.x) for one component, in place on v; with a
+// stash, the stashed partial sum (groups of four) is added
+template <int L, int H, typename ST>
+__device__ __forceinline__ void adj_products(cf* v, const float2* __restrict__ sh, int t, int pt, int tm, int comp,
+                                             const ST* add) {
+    constexpr int T = L / 16;
+#pragma unroll
+    for (int g4 = 0; g4 < 4; ++g4) {
+        cf prev[4];
+        if (add) add->load4(g4, prev);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int ka = 4 * g4 + e;
+            int idx;
+            bool direct;
+            if (ka < 8) {
+                idx = ka * T + t;
+                direct = true;
+            } else if (H == 0 && pt == 0) {
+                idx = (16 - ka) * T;
+                direct = ka == 8;
+            } else {
+                idx = (15 - ka) * T + tm;
+                direct = false;
+            }
+            const float2 q = __ldg(sh + idx);
+            const float sv = comp ? q.y : (direct ? q.x : -q.x);
+            const cf r = mk(sv * v[ka].y, sv * v[ka].x);
+            v[ka] = add ? prev[e] + r : r;
+        }
+    }
+}
+
+// pass B of the adjoint: column ky of Z_x and Z_y (natural rows) -> G column, x solve
+// applied, rows stored at the chunk-permuted positions (i % 16) (nx / 16) + i / 16.
+// Stashes: A, B in tensor memory (shared slots for 512), C in xb (shared, own slots).
+template <int L>
+__global__ void __launch_bounds__(L / 16, 2)
+    k_net_cols_adj(const cf* __restrict__ zx, const cf* __restrict__ zy, int nx, int solve,
+                   const cf* __restrict__ nb, const cf* __restrict__ tw, const float2* __restrict__ spec,
+                   cf* __restrict__ g) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    constexpr int HS = L / 2 + 2;
+    constexpr bool kTm = Stash<L>::kTmem;
+    constexpr bool kTwt = cols_twiddles_in_tmem<L>();
+    constexpr unsigned kWarpCols = kTwt ? 128 : 64;
+    constexpr unsigned kCols = kTwt ? 256 : (T > 128 ? 128 : 64);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
+    cf* xb = E + BUF;                         // stash C ([r][t]), then the solve's transposition
+    cf* edge = xb + BUF;
+    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
+    cf* sslots = reinterpret_cast<cf*>(tslot + 4);
+    const int t = threadIdx.x;
+    if constexpr (kTm) {
+        if (t < 32) tmem_alloc(tslot, kCols);
+    }
+    const int ky = blockIdx.x;
+    const int tile = ky >> 1, c = ky & 1;
+    const size_t slab = (size_t)nx * kTW;
+    const float2* se = spec + (size_t)ky * 2 * HS;
+    const float2* so = se + HS;
+    if (t == 0) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(se), "r"((unsigned)(2 * HS * sizeof(float2)))
+                     : "memory");
+    }
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    tmem_fence_before();
+    __syncthreads();  // publishes the tensor-memory address
+    tmem_fence_after();
+    const unsigned tA = kTm ? *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + kWarpCols * (unsigned)(t >> 7) : 0u;
+    const Stash<L> sA{tA, sslots, t};
+    const Stash<L> sB{tA + 32, sslots + 16 * T, t};
+    const Stash<L, false> sC{0u, xb, t};  // shared ([r][t], own slots)
+    const TmemTw<L> tt{tA + 64, tA + 96};
+    if constexpr (kTwt) {
+        cf f[16], h[16];
+        net::stage_factors<L>(bs, f, h);
+        tmem_store16(tt.a2, f);
+        tmem_store16(tt.a3, h);
+    }
+    auto FWD = [&](cf* vv) {
+        if constexpr (kTwt) net::fwd_p<L>(vv, E, tt, t);
+        else net::fwd<L>(vv, E, bs, t);
+    };
+    auto INV = [&](cf* vv) {
+        if constexpr (kTwt) net::inv_t_p<L>(vv, E, tt, t);
+        else net::inv_t<L>(vv, E, bs, t);
+    };
+    const int pt = net::perm<L>(t);
+    const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);
+    const int to = net::perm_inv<L>(T - 1 - pt);
+    const cf wt = reg::ld_tw(tw, t);
+    cf v[16];
+    auto load_col = [&](const cf* zs) {
+        const cf* zc = zs + (size_t)tile * slab + c;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            v[r] = n < nx ? ld2(zc + (size_t)n * kTW) : mk(0.f, 0.f);
+        }
+    };
+    auto twist_to = [&](const Stash<L>& st) {
+#pragma unroll
+        for (int g4 = 0; g4 < 4; ++g4) {
+            cf y[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) y[e] = cmul(v[4 * g4 + e], reg::twist(wt, 4 * g4 + e));
+            st.store4(g4, y);
+        }
+        st.store_done();
+    };
+    // g_x: even-half products into A, odd-half products into C (twisted column via B)
+    load_col(zx);
+    twist_to(sB);
+    FWD(v);
+    adj_products<L, 0>(v, se, t, pt, te, 0, (const Stash<L>*)nullptr);
+    sA.store16(v);
+    sB.load16(v);
+    __syncthreads();  // fwd then fwd on one buffer
+    FWD(v);
+    adj_products<L, 1>(v, so, t, pt, to, 0, (const Stash<L>*)nullptr);
+    sC.store16(v);
+    // g_y: add its products, transform back
+    load_col(zy);
+    twist_to(sB);
+    __syncthreads();
+    FWD(v);
+    adj_products<L, 0>(v, se, t, pt, te, 1, &sA);
+    INV(v);
+    sA.store16(v);  // u_even
+    sB.load16(v);
+    __syncthreads();
+    FWD(v);
+    adj_products<L, 1>(v, so, t, pt, to, 1, &sC);
+    INV(v);
+    // u = conj(u_even + W_2L^n u_odd), cropped to the grid
+    {
+        const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
+#pragma unroll
+        for (int g4 = 0; g4 < 4; ++g4) {
+            cf ue[4];
+            sA.load4(g4, ue);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = 4 * g4 + e;
+                const int n = t + r * T;
+                v[r] = n < nx ? conjg(ue[e] + cmulc(v[r], reg::untwist(wtc, r))) : mk(0.f, 0.f);
+            }
+        }
+    }
+    const int nact = nx >> 4;
+    cf* gc = g + (size_t)tile * slab + c;
+    if (solve) {
+        // natural-strided -> chunks through xb, x solve, rows 16 t + r stored at r (nx/16) + t
+        __syncthreads();  // every thread is done with its stash C slots in xb
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = xb[pad(16 * t + r)];
+        solve_chunk<cf>(v, t, nact, T, edge);
+        if (t < nact) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) gc[(size_t)(r * nact + t) * kTW] = v[r];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            if (n < nx) gc[(size_t)((n & 15) * nact + (n >> 4)) * kTW] = v[r];
+        }
+    }
+    if constexpr (kTm) {
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (t < 32) tmem_dealloc(*tslot, kCols);
+    }
+}
+
+template <int L>
+constexpr size_t cols_adj_smem_bytes() {
+    constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
+    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16 +
+           (Stash<L>::kTmem ? 0 : (size_t)2 * 16 * T * sizeof(cf));
+}
+
+// pass C of the adjoint: persistent over rows i of G (stored at the chunk-permuted row
+// positions); inverse row transform, crop to ny, y solve, coalesced store of the row
+template <int L>
+__global__ void __launch_bounds__(L / 16, 3)
+    k_net_rows_inv_adj(const __grid_constant__ CUtensorMap gmap, const cf* __restrict__ g, int nx, int ny,
+                       int solve, const cf* __restrict__ nb, const cf* __restrict__ tw, float* __restrict__ out,
+                       int* __restrict__ err) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* S = reinterpret_cast<cf*>(smem_raw);
+    cf* E = reinterpret_cast<cf*>(smem_raw + inv_e_offset<L>());
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(E + BUF);
+    float* edge = reinterpret_cast<float*>(bar + 1);
+    const int t = threadIdx.x;
+    int i = blockIdx.x;
+    if (i >= nx) return;
+    const int nq = nx >> 4;
+    auto rowpos = [&](int row) { return (row & 15) * nq + (row >> 4); };
+    auto issue = [&](int row) {
+        mbar_expect_tx(bar, (unsigned)(L * sizeof(cf)));
+#pragma unroll 1
+        for (int b = 0; b < L / 2 / kBox; ++b) tma_load_4d(S + 2 * b * kBox, &gmap, 0, rowpos(row), b * kBox, 0, bar);
+        S[L] = ld2(g + (size_t)(L / 2) * nx * kTW + (size_t)rowpos(row) * kTW);  // read back by thread 0 only
+    };
+    if (t == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (t == 0) issue(i);
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    const cf wt = reg::ld_tw(tw, t);
+    const int pt = net::perm<L>(t);
+    const int nact = ny >> 4;
+    unsigned ph = 0;
+    for (; i < nx; i += gridDim.x, ph ^= 1u) {
+        const int ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0);
+        if (!ok) {
+            if (t == 0) flag_error(err, TDG_ERR_TIMEOUT);
+            mbar_wait(bar, ph);
+            return;
+        }
+        cf v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int k = t + T * r;
+            v[r] = conjg(pack_c2r(S[k], S[L - k], reg::twist(wt, r)));
+        }
+        net::fwd<L>(v, E, bs, t);  // its barrier: every thread is done with S
+        if (t == 0 && i + (int)gridDim.x < nx) issue(i + gridDim.x);
+        __syncthreads();  // every half-warp is done with its slab of E
+#pragma unroll
+        for (int ka = 0; ka < 8; ++ka) E[pad(pt + T * ka)] = conjg(v[ka]);
+        __syncthreads();
+        float* row = out + (size_t)i * ny;
+        if (solve) {
+            // pairs 8 t .. 8 t + 7 = reals 16 t .. 16 t + 15 of the row
+            float x[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const cf o = E[pad(8 * t + j)];
+                x[2 * j] = o.x;
+                x[2 * j + 1] = o.y;
+            }
+            solve_chunk<float>(x, t, nact, T, edge);  // its barrier: E is read before the next fwd
+            if (t < nact) {
+                float4* dst = reinterpret_cast<float4*>(row) + 4 * t;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            }
+        } else {
+            float2* dst = reinterpret_cast<float2*>(row);
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2) {
+                const int n = t + T * c2;
+                const cf o = E[pad(n)];
+                if (2 * n < ny) dst[n] = make_float2(o.x, o.y);
+            }
+        }
+    }
+}
+
+template <int L>
+size_t inv_adj_bytes() {
+    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16 + 2 * (L / 16 / 32) * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -776,12 +1057,14 @@ EncodeTiledFn encode_fn() {
 
 // the tiled intermediate(s) as a tensor of floats {4 (one tile cell), nx rows, ntile cells,
 // ncomp}: strides 16 B, nx * 16 B, comp_bytes; box {4, 1, kBox, 1}
-cudaError_t encode_tiles(CUtensorMap* map, void* base, int nx, int ntile, int ncomp, size_t comp_bytes) {
+cudaError_t encode_tiles(CUtensorMap* map, void* base, int nx, int ntile, int ncomp, size_t comp_bytes,
+                         bool rank4 = false) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    const cuuint32_t rank = ncomp > 1 ? 4 : 3;
+    const cuuint32_t rank = (ncomp > 1 || rank4) ? 4 : 3;
     cuuint64_t dims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ntile, (cuuint64_t)ncomp};
-    cuuint64_t strides[3] = {16, (cuuint64_t)nx * 16, (cuuint64_t)comp_bytes};
+    cuuint64_t strides[3] = {16, (cuuint64_t)nx * 16,
+                             (cuuint64_t)(comp_bytes ? comp_bytes : (size_t)ntile * nx * 16)};
     cuuint32_t box[4] = {4, 1, (cuuint32_t)kBox, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
@@ -854,6 +1137,62 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
     return e;
 }
 
+template <int LX, int LY>
+cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, float* gsig, void* work,
+                        cudaStream_t s) {
+    const int hy = p.hy;
+    const int ntile = (hy + kTW - 1) / kTW;
+    const size_t n_el = (size_t)ntile * p.nx * kTW;
+    cf* zx = reinterpret_cast<cf*>(work);
+    cf* zy = zx + n_el;
+    cf* g = zy + n_el;
+    const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
+    const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
+    const int solve = p.order == 3;
+    cudaError_t e;
+    CUtensorMap zmx, zmy, gmap;
+    if ((e = encode_tiles(&zmx, zx, p.nx, ntile, 1, 0))) return e;
+    if ((e = encode_tiles(&zmy, zy, p.nx, ntile, 1, 0))) return e;
+    if ((e = encode_tiles(&gmap, g, p.nx, ntile, 1, 0, true))) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    size_t sm = rows_bytes<LY>();
+    if ((e = set_smem(k_net_rows<LY>, sm))) return e;
+    mark(p, 0, s);
+    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmx, zx);
+    if ((e = cudaGetLastError())) return e;
+    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmy, zy);
+    if ((e = cudaGetLastError())) return e;
+    mark(p, 1, s);
+    sm = cols_adj_smem_bytes<LX>();
+    if ((e = set_smem(k_net_cols_adj<LX>, sm))) return e;
+    k_net_cols_adj<LX><<<hy, LX / 16, sm, s>>>(zx, zy, p.nx, solve, bases_x(p), twx,
+                                               reinterpret_cast<const float2*>(p.spec_half), g);
+    if ((e = cudaGetLastError())) return e;
+    mark(p, 2, s);
+    sm = inv_adj_bytes<LY>();
+    if ((e = set_smem(k_net_rows_inv_adj<LY>, sm))) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv_adj<LY>, LY / 16, sm)))
+        return e;
+    const int grid = std::min(p.nx, std::max(1, per_sm) * nsm);
+    k_net_rows_inv_adj<LY><<<grid, LY / 16, sm, s>>>(gmap, g, p.nx, p.ny, solve, bases_y(p), twy, gsig, p.err);
+    e = cudaGetLastError();
+    mark(p, 3, s);
+    return e;
+}
+
+template <int LX>
+cudaError_t run_net_adj_x(const Plan& p, const float* gx, const float* gy, float* gs, void* work, cudaStream_t s) {
+    switch (len_y(p)) {
+        case 512: return run_net_adj<LX, 512>(p, gx, gy, gs, work, s);
+        case 1024: return run_net_adj<LX, 1024>(p, gx, gy, gs, work, s);
+        case 2048: return run_net_adj<LX, 2048>(p, gx, gy, gs, work, s);
+        default: return run_net_adj<LX, 4096>(p, gx, gy, gs, work, s);
+    }
+}
+
 template <int LX>
 cudaError_t run_net_x(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     switch (len_y(p)) {
@@ -915,6 +1254,16 @@ cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
         case 1024: return spectra_axis<1024>(p, s);
         case 2048: return spectra_axis<2048>(p, s);
         default: return spectra_axis<4096>(p, s);
+    }
+}
+
+cudaError_t launch_adjoint_net(const Plan& p, const float* gx, const float* gy, float* gsig, void* work,
+                               cudaStream_t s) {
+    switch (len_x(p)) {
+        case 512: return run_net_adj_x<512>(p, gx, gy, gsig, work, s);
+        case 1024: return run_net_adj_x<1024>(p, gx, gy, gsig, work, s);
+        case 2048: return run_net_adj_x<2048>(p, gx, gy, gsig, work, s);
+        default: return run_net_adj_x<4096>(p, gx, gy, gsig, work, s);
     }
 }
 

@@ -229,6 +229,9 @@ cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* wo
 
 template <typename T>
 cudaError_t launch_adjoint(const Plan& p, const T* gxin, const T* gyin, T* gsig, void* work, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (p.spec_half && p.net_tw) return launch_adjoint_net(p, gxin, gyin, gsig, work, s);
+    }
     const Tiled t = tiled_of<T>(p, p.nx);
     const size_t n_el = (size_t)p.ntile * t.slab;
     cpx<T>* zx = reinterpret_cast<cpx<T>*>(work);

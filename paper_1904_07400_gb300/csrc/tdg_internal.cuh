@@ -119,6 +119,8 @@ size_t net_fp32_spec_bytes(const Plan& p);
 cudaError_t launch_net_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                cudaStream_t s);
+cudaError_t launch_adjoint_net(const Plan& p, const float* gx, const float* gy, float* gsig, void* work,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_adjoint(const Plan& p, const T* gx, const T* gy, T* gsig, void* work,
                            cudaStream_t s);

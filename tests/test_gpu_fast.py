@@ -108,3 +108,45 @@ def test_padded_network_small_grid_vs_oracle(k):
     rx, ry = oracle_solver(nx, ny, k, dx, dy).forces(sigma)
     f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
     assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
+
+
+def _adjoint(nx, ny, k, dx, dy, prec, gx, gy):
+    import torch
+    from paper_1904_07400_gb300.api import Plan
+    p = Plan(nx, ny, k, dx, dy, precision=prec)
+    tx = torch.as_tensor(gx, dtype=p.dtype, device=p.device)
+    ty = torch.as_tensor(gy, dtype=p.dtype, device=p.device)
+    gs = p.adjoint(tx, ty)
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    return to_np(gs), p.path()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# the adjoint on the network path (same plans as the forward): against the FP64 GPU adjoint
+# (generic kernels) and, on a small grid, against the oracle's adjoint
+@pytest.mark.parametrize("shape,k", [((4096, 4096), 3), ((2048, 1024), 2), ((1024, 2048), 3), ((768, 1024), 1),
+                                     ((384, 512), 3), ((144, 2000), 2)])
+def test_network_adjoint_vs_fp64_gpu(shape, k):
+    nx, ny = shape
+    dx, dy = 1.0 / nx, 1.0 / ny
+    gx, gy = syn.adjoint_weights(nx, ny, seed=nx + k)
+    a32, path = _adjoint(nx, ny, k, dx, dy, "fp32", gx, gy)
+    assert path == 2
+    a64, _ = _adjoint(nx, ny, k, dx, dy, "fp64", gx, gy)
+    assert _rel(a32, a64) <= TOL_FP32
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_network_adjoint_vs_oracle(k):
+    nx, ny = 160, 208
+    dx, dy = 1.0 / nx, 0.6 / ny
+    rng = np.random.default_rng(30 + k)
+    gx, gy = rng.standard_normal((nx, ny)), rng.standard_normal((nx, ny))
+    ref = oracle_solver(nx, ny, k, dx, dy).adjoint(gx, gy)
+    got, path = _adjoint(nx, ny, k, dx, dy, "fp32", gx, gy)
+    assert path == 2
+    assert _rel(got, ref) <= TOL_FP32
