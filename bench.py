@@ -141,8 +141,8 @@ class Clocks:
 # (FP32 network path, 4096x4096, order 3).  Valid only for the kernel sources it was taken
 # on: reported when their SHA-256 still matches, null otherwise.
 MEASURED_TRAFFIC = {
-    ("cols_conv", 2, 4096): {"bytes": 268_988_416 + 215_674_880,
-                             "sha256": "320b6ea68e017286089d2e7919d8c13c58dbf8334e593cd54a3adcae58ab906a"},
+    ("cols_conv", 2, 4096): {"bytes": 268_923_136 + 215_729_920,
+                             "sha256": "5d412d79f3e411c4f408ccb96f78a502d77bc354145ec772715856fed3cbe40c"},
 }
 TRAFFIC_SOURCES = ("paper_1904_07400_gb300/csrc/net_fp32.cu", "paper_1904_07400_gb300/csrc/fft_net.cuh",
                    "paper_1904_07400_gb300/csrc/fft_reg.cuh")
