@@ -72,6 +72,15 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
  * returning (the FP64 temporaries are freed).  Errors: OOM, CUDA. */
 tdg_status tdg_build_kernel_tables(tdg_plan p, tdg_stream stream);
 
+/* The same build from quarter tables the caller kept (from tdg_copy_kernel_tables of an
+ * earlier plan with the same nx, ny, order, dx, dy; w^x then w^y, each nx x ny FP64
+ * row-major on the host).  The in-simulation reuse of the paper's Sec. 4.2: the tables
+ * are computed once, and a restarted run skips their quadrature (about 0.25 s at 4096^2)
+ * and only places and transforms them.  A spot check of ten entries against the table code
+ * rejects tables of another order, cell shape or grid.  Errors: INVALID_ARG (NULL
+ * arguments, tables that fail the check), OOM, CUDA. */
+tdg_status tdg_build_kernel_tables_from(tdg_plan p, const double* wx, const double* wy, tdg_stream stream);
+
 /* Bytes of device workspace a solve or adjoint of this plan needs. */
 size_t tdg_workspace_bytes(const tdg_plan p);
 

@@ -31,7 +31,8 @@ class Plan:
     """One grid (nx x ny cells of dx x dy), B-spline order 1..3, precision form."""
 
     def __init__(self, nx: int, ny: int, order: int, dx: float, dy: float, G: float = 1.0,
-                 precision: str = "fp32", device: int | torch.device = 0, build: bool = True):
+                 precision: str = "fp32", device: int | torch.device = 0, build: bool = True,
+                 tables: str | None = None):
         if precision not in native.PRECISION:
             raise ValueError(f"precision must be one of {sorted(native.PRECISION)}")
         dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
@@ -47,7 +48,9 @@ class Plan:
                     native.PRECISION[precision], dev.index)
         self._h = h
         self._built = False
-        if build:
+        if tables is not None:
+            self.build_from(tables)
+        elif build:
             self.build()
 
     @property
@@ -57,6 +60,28 @@ class Plan:
     def build(self) -> None:
         with torch.cuda.device(self.device):
             native.call("tdg_build_kernel_tables", self._h, _stream_handle(self.device))
+        self._built = True
+
+    def save_tables(self, path: str) -> None:
+        """Keep this plan's FP64 kernel tables (w^x, w^y on the quadrant of offsets) and its
+        parameters in an .npz file, for plans of later runs (any precision) to start from."""
+        import numpy as np
+        wx, wy = self.kernel_tables()
+        np.savez(path, wx=wx, wy=wy, params=np.array([self.nx, self.ny, self.order, self.dx, self.dy]))
+
+    def build_from(self, path: str) -> None:
+        """Build from tables kept by save_tables: their quadrature is skipped, only the
+        placement and the spectra are computed."""
+        import numpy as np
+        d = np.load(path)
+        want = np.array([self.nx, self.ny, self.order, self.dx, self.dy])
+        if d["params"].shape != want.shape or not np.array_equal(d["params"], want):
+            raise ValueError(f"{path} holds tables for (nx, ny, order, dx, dy) = {tuple(d['params'])}")
+        wx = np.ascontiguousarray(d["wx"], dtype=np.float64)
+        wy = np.ascontiguousarray(d["wy"], dtype=np.float64)
+        with torch.cuda.device(self.device):
+            native.call("tdg_build_kernel_tables_from", self._h, wx.ctypes.data, wy.ctypes.data,
+                        _stream_handle(self.device))
         self._built = True
 
     def info(self) -> dict:

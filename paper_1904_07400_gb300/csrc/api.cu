@@ -252,8 +252,9 @@ tdg_status tdg_set_workspace(tdg_plan h, void* ptr, size_t bytes) {
     return TDG_OK;
 }
 
-tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
-    if (!h) return TDG_ERR_INVALID_ARG;
+// the build; with wx_host / wy_host (quarter tables the caller kept) the quadrature is
+// skipped and the tables are copied in and placed
+static tdg_status build_plan(tdg_plan h, const double* wx_host, const double* wy_host, tdg_stream stream) {
     Plan& p = h->p;
     DeviceGuard g(p.device);
     if (!g.ok) return TDG_ERR_CUDA;
@@ -290,11 +291,13 @@ tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
     TDG_TRY(cudaMalloc(&p.spec, 2 * (size_t)p.hy * Px * p.elem));
     TDG_TRY(cudaMalloc(&placed_x, (size_t)Px * Py * sizeof(double)));
     TDG_TRY(cudaMalloc(&placed_y, (size_t)Px * Py * sizeof(double)));
-    TDG_TRY(cudaMalloc(&glx, R.x.size() * sizeof(double)));
-    TDG_TRY(cudaMalloc(&glw, R.w.size() * sizeof(double)));
     TDG_TRY(cudaMalloc(&scratch, scratch_bytes));
-    TDG_TRY(cudaMemcpyAsync(glx, R.x.data(), R.x.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    TDG_TRY(cudaMemcpyAsync(glw, R.w.data(), R.w.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (!wx_host) {
+        TDG_TRY(cudaMalloc(&glx, R.x.size() * sizeof(double)));
+        TDG_TRY(cudaMalloc(&glw, R.w.size() * sizeof(double)));
+        TDG_TRY(cudaMemcpyAsync(glx, R.x.data(), R.x.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        TDG_TRY(cudaMemcpyAsync(glw, R.w.data(), R.w.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     TDG_TRY(cudaMemsetAsync(placed_x, 0, (size_t)Px * Py * sizeof(double), s));
     TDG_TRY(cudaMemsetAsync(placed_y, 0, (size_t)Px * Py * sizeof(double), s));
     if (p.prec == TDG_FP64) {
@@ -304,7 +307,14 @@ tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
         TDG_TRY(launch_twiddles<float>(reinterpret_cast<cpx<float>*>(p.tw_x), Px, s));
         TDG_TRY(launch_twiddles<float>(reinterpret_cast<cpx<float>*>(p.tw_y), Py, s));
     }
-    TDG_TRY(launch_build_tables(p, p.wq, placed_x, placed_y, glx, glw, s));
+    if (wx_host) {
+        const size_t n = (size_t)p.nx * p.ny;
+        TDG_TRY(cudaMemcpyAsync(p.wq, wx_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        TDG_TRY(cudaMemcpyAsync(p.wq + n, wy_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        TDG_TRY(launch_place_tables(p, p.wq, placed_x, placed_y, s));
+    } else {
+        TDG_TRY(launch_build_tables(p, p.wq, placed_x, placed_y, glx, glw, s));
+    }
     if (p.prec == TDG_FP64)
         TDG_TRY(launch_spectra<double>(p, placed_x, placed_y, scratch, reinterpret_cast<double*>(p.spec), s));
     else
@@ -345,6 +355,35 @@ fail:
     p.work_bytes = keep_bytes;
     return from_cuda(e);
 #undef TDG_TRY
+}
+
+tdg_status tdg_build_kernel_tables(tdg_plan h, tdg_stream stream) {
+    if (!h) return TDG_ERR_INVALID_ARG;
+    return build_plan(h, nullptr, nullptr, stream);
+}
+
+tdg_status tdg_build_kernel_tables_from(tdg_plan h, const double* wx, const double* wy, tdg_stream stream) {
+    if (!h || !wx || !wy) return TDG_ERR_INVALID_ARG;
+    const Plan& p = h->p;
+    // spot check against the table code: the corners, the near field and a far entry of
+    // both components must agree (tables of another order, cell shape or size fail here);
+    // entries that vanish by symmetry are held to 1e-15 of the largest one checked
+    const int ms[5] = {0, 1, 2, p.nx - 1, p.nx / 2};
+    const int ns[5] = {1, 0, 3, p.ny - 1, p.ny / 3};
+    double ref[5][2], amax = 0.0;
+    for (int q = 0; q < 5; ++q)
+        for (int c = 0; c < 2; ++c) {
+            const int m = ms[q] < p.nx ? ms[q] : p.nx - 1, n = ns[q] < p.ny ? ns[q] : p.ny - 1;
+            if (tdg_kernel_entry_host(p.order, m, n, p.dx, p.dy, c, &ref[q][c]) != TDG_OK) return TDG_ERR_INVALID_ARG;
+            amax = fmax(amax, fabs(ref[q][c]));
+        }
+    for (int q = 0; q < 5; ++q)
+        for (int c = 0; c < 2; ++c) {
+            const int m = ms[q] < p.nx ? ms[q] : p.nx - 1, n = ns[q] < p.ny ? ns[q] : p.ny - 1;
+            const double got = (c ? wy : wx)[(size_t)m * p.ny + n];
+            if (!(fabs(got - ref[q][c]) <= 1e-12 * fabs(ref[q][c]) + 1e-15 * amax)) return TDG_ERR_INVALID_ARG;
+        }
+    return build_plan(h, wx, wy, stream);
 }
 
 static tdg_status check_solve_args(const Plan& p, const void* a, const void* b, const void* c) {

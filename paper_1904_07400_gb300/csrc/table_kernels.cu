@@ -45,6 +45,36 @@ __global__ void k_build_tables(int k, int nx, int ny, double dx, double dy, GLSe
     }
 }
 
+// the placement alone, from quarter tables already in wq (tables built earlier and kept by
+// the caller): the same four mirrored positions as k_build_tables
+__global__ void k_place_tables(int nx, int ny, const double* __restrict__ wq, double* __restrict__ px_tab,
+                               double* __restrict__ py_tab, int Px, int Py) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nx * ny) return;
+    int m = (int)(idx / ny), n = (int)(idx % ny);
+    const double wx = wq[idx];
+    const double wy = wq[(long)nx * ny + idx];
+    for (int sm = 0; sm < 2; ++sm) {
+        if (sm && m == 0) continue;
+        int im = sm ? Px - m : m;
+        for (int sn = 0; sn < 2; ++sn) {
+            if (sn && n == 0) continue;
+            int in = sn ? Py - n : n;
+            size_t o = (size_t)im * Py + in;
+            px_tab[o] = sm ? -wx : wx;
+            py_tab[o] = sn ? -wy : wy;
+        }
+    }
+}
+
+cudaError_t launch_place_tables(const Plan& p, const double* wq, double* placed_x, double* placed_y,
+                                cudaStream_t s) {
+    long n = (long)p.nx * p.ny;
+    int nt = 256;
+    k_place_tables<<<(unsigned)((n + nt - 1) / nt), nt, 0, s>>>(p.nx, p.ny, wq, placed_x, placed_y, p.ax.P, p.ay.P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_tables(const Plan& p, double* wq, double* placed_x, double* placed_y, const double* glx,
                                 const double* glw, cudaStream_t s) {
     GLSet g;

@@ -99,6 +99,8 @@ namespace tdg {
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_build_tables(const Plan& p, double* wq, double* placed_x, double* placed_y,
                                 const double* glx, const double* glw, cudaStream_t s);
+cudaError_t launch_place_tables(const Plan& p, const double* wq, double* placed_x, double* placed_y,
+                                cudaStream_t s);
 template <typename T>
 cudaError_t launch_twiddles(cpx<T>* tw, int P, cudaStream_t s);
 template <typename T>

@@ -25,6 +25,7 @@ SIGNATURES = [
     ("tdg_init", _c_int, [ctypes.POINTER(_c_void_p), _c_int, _c_int, _c_int, _c_double, _c_double,
                           _c_double, _c_int, _c_int]),
     ("tdg_build_kernel_tables", _c_int, [_c_void_p, _c_void_p]),
+    ("tdg_build_kernel_tables_from", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_workspace_bytes", _c_size_t, [_c_void_p]),
     ("tdg_set_workspace", _c_int, [_c_void_p, _c_void_p, _c_size_t]),
     ("tdg_solve_forces", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),

@@ -155,3 +155,21 @@ def test_kernel_entry_host_symmetries(lib):
         assert e(k, 3, 5, 1.0, 1.0, 0) == e(k, 3, -5, 1.0, 1.0, 0)
         assert e(k, 3, 5, 1.0, 1.0, 1) == e(k, 5, 3, 1.0, 1.0, 0)
         assert e(k, 0, 7, 1.0, 1.0, 0) == 0.0
+
+
+def test_build_from_tables_rejects_foreign_tables(lib):
+    # the spot check runs before any device work: tables of another order or grid, or
+    # missing arrays, are refused with INVALID_ARG
+    nx, ny = 12, 10
+    st, h = _init(lib, nx, ny, 3, 0.1, 0.1, 1.0, 1, 0)
+    assert st == 0
+    wx = np.zeros((nx, ny))
+    wy = np.zeros((nx, ny))
+    assert lib.tdg_build_kernel_tables_from(h, wx.ctypes.data, wy.ctypes.data, None) == 1
+    for m in range(nx):  # order-2 entries for an order-3 plan
+        for n in range(ny):
+            wx[m, n] = native.kernel_entry_host(2, m, n, 0.1, 0.1, 0)
+            wy[m, n] = native.kernel_entry_host(2, m, n, 0.1, 0.1, 1)
+    assert lib.tdg_build_kernel_tables_from(h, wx.ctypes.data, wy.ctypes.data, None) == 1
+    assert lib.tdg_build_kernel_tables_from(h, None, wy.ctypes.data, None) == 1
+    lib.tdg_destroy(h)
