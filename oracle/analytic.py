@@ -9,8 +9,18 @@ the same pattern (inside: (pi^2 G sigma_0 / 2) eta^(-(2n-1)) P_n(eta); outside: 
 sqrt combination whose small-eta expansion has no eta^1 ... eta^(2n-1) terms) and is
 pinned in tests against a direct elliptic-integral quadrature of the disk potential.
 All forms are attractive (F_R < 0), with F = G x (the convolution), Sec. 1.
+
+D_5 and D_6 (exponents 9/2 and 11/2, the smooth disks that show orders 4 and 5) follow
+the same rule, written out in ``rule_coefficients``: inside, F_R is
+(pi^2 G sigma_0 / 2) c_n d/ds 2F1(-n, 1/2; 1; s^2) with s = R / a and
+c_n = 2 binom(2n, n) / 4^n; outside, Q_n cancels the eta^1 ... eta^(2n-1) Taylor terms of
+P_n(eta) asin(eta) / sqrt(1 - eta^2).  The rule reproduces the printed D_3 and D_4
+coefficients exactly (tests), and D_5, D_6 are pinned by the same potential quadrature.
 """
 from __future__ import annotations
+
+from fractions import Fraction
+from math import comb, factorial
 
 import mpmath as mp
 import numpy as np
@@ -32,12 +42,42 @@ _OUTSIDE_SQRT = {
 }
 
 
+def rule_coefficients(n: int) -> tuple[dict, dict]:
+    """(P_n, Q_n) by power, exact rationals, from the hypergeometric rule above."""
+    c_n = Fraction(2 * comb(2 * n, n), 4 ** n)
+    inside = {}
+    for j in range(1, n + 1):
+        # a_j = (-n)_j (1/2)_j / (j!)^2, the coefficient of x^j in 2F1(-n, 1/2; 1; x)
+        a = Fraction(1)
+        for i in range(j):
+            a *= Fraction(-n + i) * (Fraction(1, 2) + i)
+        a /= factorial(j) ** 2
+        inside[2 * (n - j)] = c_n * 2 * j * a
+    # asin(eta) / sqrt(1 - eta^2) = sum_i 4^i (i!)^2 / (2i + 1)! eta^(2i + 1)
+    outside = {}
+    for p_pow, pc in inside.items():
+        for i in range(n):
+            deg = p_pow + 2 * i + 1
+            if deg <= 2 * n - 1:
+                outside[deg] = outside.get(deg, Fraction(0)) - pc * Fraction(4 ** i * factorial(i) ** 2,
+                                                                              factorial(2 * i + 1))
+    return inside, {q: v for q, v in outside.items() if v != 0}
+
+
+def _coefs(n: int) -> tuple[dict, dict]:
+    if n in _INSIDE:
+        return _INSIDE[n], _OUTSIDE_SQRT[n]
+    ins, out = rule_coefficients(n)
+    return {q: float(v) for q, v in ins.items()}, {q: float(v) for q, v in out.items()}
+
+
 def _poly(coefs: dict, x):
     return sum(c * x ** p for p, c in coefs.items())
 
 
 def radial_force(n: int, R, a: float, sigma0: float = 1.0, G: float = 1.0):
-    """F_R of the D_n disk at z = 0 (Sec. 3 for n = 3, 4; derived n = 2; classic n = 1).
+    """F_R of the D_n disk at z = 0 (Sec. 3 for n = 3, 4; derived n = 2 and n >= 5; classic
+    n = 1).
 
     D_1 reduces to the classic Maclaurin disk, F_R = -pi^2 G sigma_0 R / (2 a) inside.
     """
@@ -45,12 +85,13 @@ def radial_force(n: int, R, a: float, sigma0: float = 1.0, G: float = 1.0):
     eta = a / R
     p = 2 * n - 1
     out = np.empty_like(R)
+    ins, outs = _coefs(n)
     inside = eta >= 1.0
     e = eta[inside]
-    out[inside] = (_PI ** 2 * sigma0 * G / 2.0) * e ** (-p) * _poly(_INSIDE[n], e)
+    out[inside] = (_PI ** 2 * sigma0 * G / 2.0) * e ** (-p) * _poly(ins, e)
     e = eta[~inside]
     out[~inside] = _PI * sigma0 * G * e ** (-p) * (
-        _poly(_INSIDE[n], e) * np.arcsin(e) + _poly(_OUTSIDE_SQRT[n], e) * np.sqrt(1.0 - e * e))
+        _poly(ins, e) * np.arcsin(e) + _poly(outs, e) * np.sqrt(1.0 - e * e))
     # far outside the disk the two outside terms cancel to O(eta^(2n+1)): evaluate there
     # with 50 digits (the loss is about eta^-(2n+1) ulp)
     far = eta < 0.35
@@ -60,10 +101,13 @@ def radial_force(n: int, R, a: float, sigma0: float = 1.0, G: float = 1.0):
 
 
 def _outside_mp(n: int, eta: float, sigma0: float, G: float) -> float:
+    ci, co = (_INSIDE[n], _OUTSIDE_SQRT[n]) if n in _INSIDE else rule_coefficients(n)
     with mp.workdps(50):
         e = mp.mpf(eta)
-        ins = sum(mp.mpf(c) * e ** q for q, c in _INSIDE[n].items())
-        out = sum(mp.mpf(c) * e ** q for q, c in _OUTSIDE_SQRT[n].items())
+        ins = sum(mp.mpf(c.numerator) / c.denominator * e ** q if isinstance(c, Fraction) else mp.mpf(c) * e ** q
+                  for q, c in ci.items())
+        out = sum(mp.mpf(c.numerator) / c.denominator * e ** q if isinstance(c, Fraction) else mp.mpf(c) * e ** q
+                  for q, c in co.items())
         return float(mp.pi * sigma0 * G * e ** (-(2 * n - 1)) * (ins * mp.asin(e) + out * mp.sqrt(1 - e * e)))
 
 

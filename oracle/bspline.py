@@ -60,13 +60,55 @@ def _poly_on_interval(k: int, i: int, knots, j: int) -> Polynomial:
     return left + right
 
 
-def pieces(k: int) -> list[tuple[float, float, Polynomial]]:
-    """The k polynomial pieces (lo, hi, p) of b_k, p valid on [lo, hi)."""
-    knots = centred_knots(k)
-    out = []
-    for j in range(k):
-        out.append((float(knots[j]), float(knots[j + 1]), _poly_on_interval(k, 0, knots, j)))
+def _padd(a: list, b: list) -> list:
+    n = max(len(a), len(b))
+    return [(a[i] if i < len(a) else 0) + (b[i] if i < len(b) else 0) for i in range(n)]
+
+
+def _pmul(a: list, b: list) -> list:
+    out = [Fraction(0)] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        for j, y in enumerate(b):
+            out[i + j] += x * y
     return out
+
+
+def _exact_on_interval(k: int, i: int, knots, j: int) -> list[Fraction]:
+    """Coefficients (by power) of B^[k]_i on [t_j, t_{j+1}), in exact rationals: the same
+    recursion Eq. (eqnBk) on polynomials with Fraction coefficients."""
+    if k == 1:
+        return [Fraction(1 if i == j else 0)]
+    ti, tik1 = knots[i], knots[i + k - 1]
+    ti1, tik = knots[i + 1], knots[i + k]
+    left = _pmul([-ti / (tik1 - ti), 1 / (tik1 - ti)], _exact_on_interval(k - 1, i, knots, j))
+    right = _pmul([tik / (tik - ti1), -1 / (tik - ti1)], _exact_on_interval(k - 1, i + 1, knots, j))
+    return _padd(left, right)
+
+
+def pieces_exact(k: int) -> list[tuple[Fraction, Fraction, list[Fraction]]]:
+    """The k pieces (lo, hi, coefficients by power of t) of b_k in exact rationals.  Orders
+    4 and 5 have coefficients that are not binary fractions, so routes that compose the
+    pieces with large offsets start from these, not from their FP64 roundings."""
+    knots = centred_knots(k)
+    return [(knots[j], knots[j + 1], _exact_on_interval(k, 0, knots, j)) for j in range(k)]
+
+
+def pieces(k: int) -> list[tuple[float, float, Polynomial]]:
+    """The k polynomial pieces (lo, hi, p) of b_k, p valid on [lo, hi) (FP64 coefficients,
+    each the rounding of the exact rational)."""
+    return [(float(lo), float(hi), Polynomial([float(c) for c in cs])) for lo, hi, cs in pieces_exact(k)]
+
+
+def eval_exact(k: int, t: float) -> float:
+    """b_k(t) for a float t, evaluated in exact rationals and rounded once."""
+    ft = Fraction(t)
+    for lo, hi, cs in pieces_exact(k):
+        if lo <= ft < hi:
+            acc = Fraction(0)
+            for c in reversed(cs):
+                acc = acc * ft + c
+            return float(acc)
+    return 0.0
 
 
 def values_at_integers(k: int) -> dict[int, float]:

@@ -41,7 +41,7 @@ import mpmath as mp
 import numpy as np
 from numpy.polynomial import Polynomial
 
-from .bspline import pieces
+from .bspline import eval_exact, pieces, pieces_exact
 
 # ----------------------------------------------------------------------------------
 # Route P: the paper's closed forms (Eqs. intF, G_function, intMoment, B11-B13)
@@ -83,16 +83,42 @@ def F_tilde(xl, xr, yl, yr, alpha: int, beta: int):
             - F_anti(xr, yl, alpha, beta) + F_anti(xl, yl, alpha, beta))
 
 
+class _MPoly:
+    """Polynomial with mpmath coefficients, by power."""
+
+    def __init__(self, coef):
+        self.coef = list(coef)
+
+
+def _mpf(fr) -> mp.mpf:
+    return mp.mpf(fr.numerator) / fr.denominator
+
+
+def _compose(cs, m: int, h: float) -> list:
+    """Coefficients (by power of u) of p(u/h + m) for p given by exact rationals cs, in
+    mpmath at the working precision (Horner on polynomials)."""
+    a, s = mp.mpf(m), 1 / mp.mpf(h)
+    acc = [mp.mpf(0)]
+    for c in reversed(cs):
+        nxt = [mp.mpf(0)] * (len(acc) + 1)
+        for i, x in enumerate(acc):
+            nxt[i] += x * a
+            nxt[i + 1] += x * s
+        nxt[0] += _mpf(c)
+        acc = nxt
+    return acc[:len(cs)]
+
+
 def _rect_polys(k: int, m: int, h: float):
-    """Pieces of b_k(u/h + m) as (u_lo, u_hi, polynomial in u) with exact-ish coefficients.
+    """Pieces of b_k(u/h + m) as (u_lo, u_hi, polynomial in u), composed in mpmath from the
+    exact rational pieces.
 
     Composition t = u/h + m of the unit-spacing pieces (Sec. 2.2: the rectangles of
     Cases 1-3 are the knot intervals of the shifted splines).
     """
     out = []
-    for lo, hi, p in pieces(k):
-        q = p(Polynomial([float(m), 1.0 / h]))
-        out.append(((lo - m) * h, (hi - m) * h, q))
+    for lo, hi, cs in pieces_exact(k):
+        out.append(((_mpf(lo) - m) * mp.mpf(h), (_mpf(hi) - m) * mp.mpf(h), _MPoly(_compose(cs, m, h))))
     return out
 
 
@@ -165,13 +191,13 @@ def _inner_ibp(k: int, m: int, h: float, v):
         a1 = (0.5 - m) * h
         return 1 / mp.sqrt(a0 * a0 + v * v) - 1 / mp.sqrt(a1 * a1 + v * v)
     total = mp.mpf(0)
-    for lo, hi, p in pieces(k):
-        dp = p.deriv()
-        q = dp(Polynomial([float(m), 1.0 / h]))  # b'(u/h + m) as a polynomial in u
-        ul, uh = mp.mpf((lo - m) * h), mp.mpf((hi - m) * h)
-        for j, c in enumerate(q.coef):
-            if c != 0.0:
-                total += mp.mpf(c) / h * (_J(j, uh, v) - _J(j, ul, v))
+    for lo, hi, cs in pieces_exact(k):
+        dcs = [i * c for i, c in enumerate(cs)][1:]
+        q = _compose(dcs, m, h)  # b'(u/h + m) as a polynomial in u
+        ul, uh = (_mpf(lo) - m) * mp.mpf(h), (_mpf(hi) - m) * mp.mpf(h)
+        for j, c in enumerate(q):
+            if c != 0:
+                total += c / h * (_J(j, uh, v) - _J(j, ul, v))
     return total
 
 
@@ -182,20 +208,21 @@ def w_route_i(k: int, m: int, n: int, dx: float, dy: float, component: str = "x"
         return w_route_i(k, n, m, dy, dx, "x", dps)
     with mp.workdps(dps):
         total = mp.mpf(0)
-        for lo, hi, p in pieces(k):
-            vl, vh = (lo - n) * dy, (hi - n) * dy
-            pts = [mp.mpf(vl), mp.mpf(vh)]
-            if vl < 0.0 < vh:
-                pts = [mp.mpf(vl), mp.mpf(0), mp.mpf(vh)]
+        for lo, hi, cs in pieces_exact(k):
+            vl, vh = (_mpf(lo) - n) * mp.mpf(dy), (_mpf(hi) - n) * mp.mpf(dy)
+            pts = [vl, vh]
+            if vl < 0 < vh:
+                pts = [vl, mp.mpf(0), vh]
+            pv = _MPoly(_compose(cs, n, dy))  # b(v/dy + n) as a polynomial in v
 
-            def f(v, p=p):
-                return _poly_mp(p, v / dy + n) * _inner_ibp(k, m, dx, v)
+            def f(v, pv=pv):
+                return _poly_mp(pv, v) * _inner_ibp(k, m, dx, v)
 
             total += mp.quad(f, pts)
         return total
 
 
-def _poly_mp(p: Polynomial, t):
+def _poly_mp(p, t):
     acc = mp.mpf(0)
     for c in reversed(p.coef):
         acc = acc * t + mp.mpf(c)
@@ -237,6 +264,7 @@ def w_brute(k: int, m: int, n: int, dx: float, dy: float, component: str = "x", 
 # ----------------------------------------------------------------------------------
 
 
+@functools.lru_cache(maxsize=None)
 def _gl_nodes(k: int, q: int):
     """Nodes t_a and weights b_k(t_a) * gl_a over the k pieces of b_k."""
     x, wgl = np.polynomial.legendre.leggauss(q)
@@ -244,7 +272,7 @@ def _gl_nodes(k: int, q: int):
     for lo, hi, p in pieces(k):
         t = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
         ts.append(t)
-        ws.append(0.5 * (hi - lo) * wgl * p(t))
+        ws.append(0.5 * (hi - lo) * wgl * np.array([eval_exact(k, ti) for ti in t]))
     return np.concatenate(ts), np.concatenate(ws)
 
 
@@ -272,6 +300,19 @@ NEAR_FIELD = 4  # index distance max(|m|, |n|) below which route I is used
 FAR_BANDS = ((1, 32), (2, 24), (4, 16), (8, 10), (16, 7), (64, 5), (None, 4))
 
 
+def near_field_size(k: int) -> int:
+    """Index distance below which route I is used.  Orders above 3 have wider supports,
+    so their nearest polynomial piece sits (k - 3)/2 cells closer to the origin."""
+    return NEAR_FIELD + max(0, k - 3)
+
+
+def band_distance(k: int, m, n, dx: float, dy: float):
+    """Distance that selects the Gauss-Legendre band: the effective distance less the
+    (k - 3)/2 cells by which the support of orders above 3 reaches closer to the origin
+    (orders 4, 5 measured against route I like orders 1-3)."""
+    return effective_distance(m, n, dx, dy) - max(0, k - 3) / 2.0
+
+
 def effective_distance(m, n, dx: float, dy: float):
     """Distance of offset (m, n) in units of the longer cell side.  Gauss-Legendre
     convergence on a piece depends on its distance from the origin over its width, so
@@ -283,7 +324,11 @@ def effective_distance(m, n, dx: float, dy: float):
 def _near_entry(k: int, m: int, n: int, ratio: float, component: str) -> float:
     if (component == "x" and m == 0) or (component == "y" and n == 0):
         return 0.0  # odd in the force direction
-    return float(w_route_i(k, m, n, 1.0, ratio, component, dps=20))
+    if component == "y":
+        # w^y(m, n; 1, ratio) = w^x(n, m; ratio, 1) = w^x(n, m; 1, 1/ratio) (scale
+        # invariance), so square cells share one set of entries
+        return _near_entry(k, n, m, 1.0 / ratio, "x")
+    return float(w_route_i(k, m, n, 1.0, ratio, "x", dps=20))
 
 
 def kernel_table_quarter(k: int, nx: int, ny: int, dx: float, dy: float, component: str = "x",
@@ -293,16 +338,17 @@ def kernel_table_quarter(k: int, nx: int, ny: int, dx: float, dy: float, compone
     out = np.zeros((nx, ny))
     # near field by route I; w depends on the cells only through dy/dx (scale invariance
     # of u r^-3 du dv), so those entries are cached per (k, m, n, dy/dx)
-    for m in range(min(nx, NEAR_FIELD)):
-        for n in range(min(ny, NEAR_FIELD)):
+    nf = near_field_size(k)
+    for m in range(min(nx, nf)):
+        for n in range(min(ny, nf)):
             out[m, n] = _near_entry(k, m, n, dy / dx, component)
     mm_all = np.arange(nx)
     nn_all = np.arange(ny)
     for m0 in range(0, nx, chunk):
         mm = mm_all[m0:m0 + chunk, None]
         nn = nn_all[None, :]
-        d = effective_distance(mm, nn, dx, dy)
-        near = np.maximum(mm, nn) < NEAR_FIELD
+        d = band_distance(k, mm, nn, dx, dy)
+        near = np.maximum(mm, nn) < nf
         block = np.zeros(d.shape)
         lower = 0.0
         for limit, q in FAR_BANDS:

@@ -3,8 +3,8 @@ import numpy as np
 import pytest
 import scipy.linalg
 
-from oracle.bspline import b, pieces, weight_matrix
-from oracle.coefficients import apply_interpolation, bspline_coefficients, thomas
+from oracle.bspline import b, pieces, pieces_exact, weight_matrix
+from oracle.coefficients import apply_interpolation, banded_solve, bspline_coefficients, stencil, thomas
 
 
 def test_weight_matrix_matches_paper():
@@ -13,7 +13,7 @@ def test_weight_matrix_matches_paper():
     np.testing.assert_allclose(weight_matrix(), printed, rtol=0, atol=1e-16)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_partition_of_unity_and_unit_mass(k):
     rng = np.random.default_rng(0)
     for t in rng.uniform(-3, 3, 50):
@@ -24,7 +24,7 @@ def test_partition_of_unity_and_unit_mass(k):
     assert abs(total - 1.0) < 1e-15
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_smoothness_at_knots(k):
     # Sec. 2: distinct knots -> the first k-2 derivatives are continuous (C^{k-2})
     ps = pieces(k)
@@ -37,7 +37,7 @@ def test_smoothness_at_knots(k):
         assert abs(ps[-1][2].deriv(d)(ps[-1][1])) < 1e-13
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_bspline_is_repeated_box_convolution(k):
     # textbook identity for cardinal splines: b_k(t) = int_{-1/2}^{1/2} b_{k-1}(t - s) ds
     import scipy.integrate
@@ -87,3 +87,54 @@ def test_interpolation_stencil_is_weight_matrix():
     s = apply_interpolation(c, 3)
     np.testing.assert_allclose(s[2:5, 2:5], weight_matrix(), atol=1e-17)
     assert np.count_nonzero(s) == 9
+
+
+# --------------------------------------------------------------------------------------
+# Orders 4 and 5: the same interpolation condition with wider stencils
+# --------------------------------------------------------------------------------------
+
+def test_stencils_orders_4_5_are_the_cardinal_values():
+    # cardinal cubic and quartic B-splines at the integers (Euler-Frobenius numbers):
+    # (1, 4, 1)/6 and (1, 76, 230, 76, 1)/384
+    np.testing.assert_allclose(stencil(4), np.array([1, 4, 1]) / 6.0, rtol=0, atol=2e-16)
+    np.testing.assert_allclose(stencil(5), np.array([1, 76, 230, 76, 1]) / 384.0, rtol=0, atol=2e-16)
+    assert stencil(3) == [0.125, 0.75, 0.125]
+    # the exact rational pieces: b_5 on its first interval is (t + 5/2)^4 / 24
+    from fractions import Fraction as Fr
+    lo, hi, cs = pieces_exact(5)[0]
+    assert (lo, hi) == (Fr(-5, 2), Fr(-3, 2))
+    assert cs == [Fr(625, 384), Fr(125, 48), Fr(25, 16), Fr(5, 12), Fr(1, 24)]
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_banded_solve_matches_lapack(k):
+    st = stencil(k)
+    h = (len(st) - 1) // 2
+    rng = np.random.default_rng(k)
+    for n in (1, 2, 3, 4, 17, 200):
+        rhs = rng.standard_normal((n, 3))
+        ab = np.zeros((2 * h + 1, n))
+        for d in range(-h, h + 1):
+            # LAPACK band storage: ab[h + i - j, j] = A[i, j]; diagonal i - j = -d holds st[d + h]
+            row = h - d
+            if d >= 0:
+                ab[row, d:] = st[d + h]
+            else:
+                ab[row, :n + d] = st[d + h]
+        ref = scipy.linalg.solve_banded((h, h), ab, rhs)
+        np.testing.assert_allclose(banded_solve(st, rhs), ref, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("shape", [(1, 3), (3, 4), (6, 5), (11, 9)])
+def test_coefficient_solve_orders_4_5_by_direct_evaluation(k, shape):
+    # the interpolation condition itself: sum_{i'j'} C b_k(i - i') b_k(j - j') = sigma at every
+    # cell centre, the spline values taken from the recursive definition (C = 0 outside)
+    rng = np.random.default_rng(7 + k)
+    sigma = rng.standard_normal(shape)
+    c = bspline_coefficients(sigma, k)
+    nx, ny = shape
+    bx = np.array([[b(k, float(i - a)) for a in range(nx)] for i in range(nx)])
+    by = np.array([[b(k, float(j - a)) for a in range(ny)] for j in range(ny)])
+    np.testing.assert_allclose(bx @ c @ by.T, sigma, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(apply_interpolation(c, k), sigma, rtol=0, atol=1e-13)

@@ -13,7 +13,7 @@ def _rand(shape, seed):
 
 
 @pytest.mark.parametrize("k,nx,ny,dy", [(1, 9, 9, 1.0), (2, 12, 20, 1.0), (3, 16, 16, 1.0),
-                                        (3, 11, 7, 0.5), (2, 5, 13, 2.0)])
+                                        (3, 11, 7, 0.5), (2, 5, 13, 2.0), (4, 10, 13, 1.0), (5, 12, 9, 1.0)])
 def test_fft_equals_direct_sum(k, nx, ny, dy):
     wx, wy = kt.kernel_tables(k, nx, ny, 1.0, dy)
     c = _rand((nx, ny), k)
@@ -42,7 +42,7 @@ def test_direct_sum_against_definition_loop():
             assert abs(sx - fx[i, j]) < 1e-14 and abs(sy - fy[i, j]) < 1e-14
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_invariants(k):
     n = 24
     S = Solver(n, n, k, 1.0 / n, 1.0 / n)
@@ -82,7 +82,7 @@ def test_translation_equivariance(k):
     np.testing.assert_allclose(gy[10:40, 10:40], np.roll(fy, (1, -1), axis=(0, 1))[10:40, 10:40], atol=tol)
 
 
-@pytest.mark.parametrize("k", [1, 3])
+@pytest.mark.parametrize("k", [1, 3, 4, 5])
 def test_adjoint_identities(k):
     nx, ny = 20, 14
     S = Solver(nx, ny, k, 1.0 / nx, 1.0 / nx)

@@ -224,3 +224,88 @@ def test_assembled_table_symmetries():
     for (m, n) in [(1, 1), (3, -4), (-5, 8), (2, 0)]:
         ref = float(kt.w_route_i(2, m, n, 0.2, 0.1, "y"))
         assert abs(wy2[m + 5, n + 8] - ref) < 4e-15 * abs(ref) + 1e-18
+
+
+# --------------------------------------------------------------------------------------
+# Orders 4 and 5 (the extension the paper calls straightforward)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k,m,n,comp", [(4, 3, 3, "x"), (4, -4, 5, "y"), (5, 3, 4, "x"), (5, 4, -3, "y"),
+                                        (5, 9, 4, "x")])
+def test_route_p_equals_route_i_orders_4_5(k, m, n, comp):
+    # the paper's monomial expansion (now with alpha + beta up to 5, via Eq. intMoment)
+    # against integration by parts
+    assert kt.route_p_valid(k, m, n)
+    p = kt.w_route_p(k, m, n, 1.0, 1.0, comp)
+    i = kt.w_route_i(k, m, n, 1.0, 1.0, comp, dps=25)
+    assert abs(p - i) < mp.mpf(10) ** -18 * abs(p)
+
+
+@pytest.mark.parametrize("k,m,n", [(4, 3, 3), (5, 4, 3)])
+def test_route_i_equals_brute_force_orders_4_5(k, m, n):
+    ref = kt.w_brute(k, m, n, 1.0, 0.5, "x", dps=15)
+    got = kt.w_route_i(k, m, n, 1.0, 0.5, "x", dps=20)
+    assert abs(ref - got) < 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_near_origin_orders_4_5(k):
+    assert abs(kt.w_route_i(k, 0, 1, 1.0, 1.0)) < 1e-25
+    assert kt.w_route_i(k, 1, 0, 1.0, 1.0) < 0
+    a = kt.w_route_i(k, 2, 1, 0.25, 0.5)
+    b_ = kt.w_route_i(k, 2, 1, 1.0, 2.0)
+    assert abs(a - b_) < 1e-20
+    assert abs(kt.w_route_i(k, 1, 2, 1.0, 1.0, "y") - kt.w_route_i(k, 2, 1, 1.0, 1.0, "x")) < 1e-20
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("dy", [1.0, 0.125])
+def test_far_field_bands_reach_fp64_orders_4_5(k, dy):
+    # the nearest offsets of the bands that orders 4, 5 reach (the band distance is shifted
+    # by (k - 3)/2 cells and the near field widened by k - 3)
+    dx = 1.0
+    nf = kt.near_field_size(k)
+    checked = 0
+    for (m, n) in [(nf, 0), (1, nf), (nf, nf), (0, nf + 2), (12, 3), (33, 0)]:
+        d = float(kt.band_distance(k, m, n, dx, dy))
+        q = [q for lim, q in kt.FAR_BANDS if lim is None or d < lim][0]
+        for comp in ("x", "y"):
+            if (comp == "x" and m == 0) or (comp == "y" and n == 0):
+                continue
+            ref = float(kt.w_route_i(k, m, n, dx, dy, comp, dps=25))
+            got = kt.w_far_gl(k, np.array([m]), np.array([n]), dx, dy, q, comp)[0]
+            assert abs(got - ref) < 2e-14 * abs(ref), (k, m, n, comp, q)
+            checked += 1
+    assert checked >= 8
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_far_field_second_moment_expansion(k):
+    # far from the origin the spline acts through its moments: mass 1, mean 0, variance
+    # k/12 per axis, so w = dx dy [f + (k/24)(dx^2 f_uu + dy^2 f_vv)] + O(d^-7) with
+    # f = u r^-3 at the spline's centre (u, v) = (-m dx, -n dy); a dropped or wrong piece
+    # of b_k changes the mass or the variance and fails this
+    dx, dy = 1.0, 0.75
+    for (m, n) in [(400, 150), (-300, 420), (90, -500)]:
+        u, v = -m * dx, -n * dy
+        r2 = u * u + v * v
+        r = np.sqrt(r2)
+        f = u / r ** 3
+        fuu = -9 * u / r ** 5 + 15 * u ** 3 / r ** 7
+        fvv = -3 * u / r ** 5 + 15 * u * v * v / r ** 7
+        ref = dx * dy * (f + k / 24.0 * (dx * dx * fuu + dy * dy * fvv))
+        got = kt.w_far_gl(k, np.array([m]), np.array([n]), dx, dy, 5, "x")[0]
+        assert abs(got - ref) < 1e-9 * abs(ref), (k, m, n, got, ref)
+        # the correction term itself is needed (it is ~1e-5 of f here)
+        assert abs(got - dx * dy * f) > 1e3 * abs(got - ref)
+
+
+def test_assembled_table_orders_4_5_against_route_i():
+    # near field (route I) and far bands assembled, square cells, against route I
+    for k in (4, 5):
+        wx, wy = kt.kernel_tables(k, 9, 11, 0.1, 0.1)
+        for (m, n) in [(1, 1), (3, -4), (-7, 8), (8, 10)]:
+            refx = float(kt.w_route_i(k, m, n, 0.1, 0.1, "x", dps=20))
+            refy = float(kt.w_route_i(k, m, n, 0.1, 0.1, "y", dps=20))
+            assert abs(wx[m + 8, n + 10] - refx) < 2e-14 * abs(refx) + 1e-18
+            assert abs(wy[m + 8, n + 10] - refy) < 2e-14 * abs(refy) + 1e-18
