@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="fp32,fp32_tc16,fp64")
     ap.add_argument("--size", type=int, default=N_GRID)
+    ap.add_argument("--order", type=int, default=ORDER, choices=[1, 2, 3, 4, 5],
+                    help="B-spline order of the solve (the headline workload is order 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-depth", type=int, default=3,
                     help="end-to-end steps in flight (one stream and workspace each)")
@@ -522,9 +524,13 @@ E2E_DEPTH = 3
 
 
 def main():
-    global E2E_DEPTH
+    global E2E_DEPTH, ORDER, METRIC, WORKLOAD
     args = parse()
     E2E_DEPTH = args.e2e_depth
+    if args.order != ORDER:
+        METRIC = METRIC.replace("order-3", f"order-{args.order}")
+        WORKLOAD = WORKLOAD.replace("order-3", f"order-{args.order}")
+        ORDER = args.order
     if args.batched:
         run_batched(args)
         return

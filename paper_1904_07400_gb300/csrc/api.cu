@@ -202,10 +202,10 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
                     tdg_precision prec, int device) {
     if (!out) return TDG_ERR_INVALID_ARG;
     *out = nullptr;
-    if (order < 1 || order > 3 || nx < 1 || ny < 1) return TDG_ERR_INVALID_ARG;
+    if (order < 1 || order > 5 || nx < 1 || ny < 1) return TDG_ERR_INVALID_ARG;
     if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy) || !isfinite(G)) return TDG_ERR_INVALID_ARG;
     if (prec != TDG_FP64 && prec != TDG_FP32 && prec != TDG_FP32_TC16) return TDG_ERR_INVALID_ARG;
-    if (prec == TDG_FP32_TC16 && !tc16_available(nx, ny)) return TDG_ERR_UNSUPPORTED;
+    if (prec == TDG_FP32_TC16 && (!tc16_available(nx, ny) || order > 3)) return TDG_ERR_UNSUPPORTED;
     if (device < 0) return TDG_ERR_INVALID_ARG;
     if (nx > kMaxN || ny > kMaxN) return TDG_ERR_UNSUPPORTED;
     tdg_plan_s* h = new (std::nothrow) tdg_plan_s();
@@ -223,7 +223,7 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
     // FP32 grids whose sides are multiples of 16 from 128 to 4096 cells run the transform
     // network, whose lengths are 512 .. 4096: pad to twice that length (any padded period
     // of at least 2n - 1 gives the same cropped result)
-    const bool net = prec == TDG_FP32 && net_fp32_length(nx) && net_fp32_length(ny);
+    const bool net = prec == TDG_FP32 && order <= 3 && net_fp32_length(nx) && net_fp32_length(ny);
     p.ax = make_axis(nx, net ? net_fp32_length(nx) : 0);
     p.ay = make_axis(ny, net ? net_fp32_length(ny) : 0);
     p.hy = p.ay.P / 2 + 1;
@@ -463,7 +463,7 @@ tdg_status tdg_copy_kernel_tables(const tdg_plan h, double* wx, double* wy) {
 }
 
 tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy, int component, double* out) {
-    if (!out || order < 1 || order > 3 || component < 0 || component > 1) return TDG_ERR_INVALID_ARG;
+    if (!out || order < 1 || order > 5 || component < 0 || component > 1) return TDG_ERR_INVALID_ARG;
     if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy)) return TDG_ERR_INVALID_ARG;
     if (component == 1) {  // w^y(m, n; dx, dy) = w^x(n, m; dy, dx)
         int t = m;

@@ -210,7 +210,7 @@ bool smooth_radices(int L, int pref, FftPlan& fp) {
 size_t row_bytes(int M, int ncols, int solve) {
     const int TR = RowCfg<float>::TR;
     return (size_t)(M + 1) * TR * sizeof(cpx<float>) + (solve ? (size_t)ncols * TR * sizeof(float) : 0) +
-           kLamTable * sizeof(float);
+           kSolveTab * sizeof(float);
 }
 
 tdg_status batch_configure(tdg_batch_s* b) {
@@ -223,8 +223,8 @@ tdg_status batch_configure(tdg_batch_s* b) {
         if (!smooth_radices(p.ay.P / 2, b->radix_pref, g.rows) || !smooth_radices(p.ax.P, b->radix_pref, g.cols))
             return TDG_ERR_UNSUPPORTED;
         const int M = p.ay.P / 2;
-        smem = std::max(smem, row_bytes(M, p.ny, p.order == 3));
-        smem = std::max(smem, (size_t)p.ax.P * sizeof(cpx<float>) + kLamTable * sizeof(float));
+        smem = std::max(smem, row_bytes(M, p.ny, solve_order(p)));
+        smem = std::max(smem, (size_t)p.ax.P * sizeof(cpx<float>) + kSolveTab * sizeof(float));
         // every pass must be covered by the block: the stages hold kEPT values per thread
         if ((long)RowCfg<float>::TR * M > (long)kBatchEPT * b->threads || p.ax.P > kBatchEPT * b->threads)
             return TDG_ERR_UNSUPPORTED;
@@ -350,7 +350,7 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
         g.nx = p.nx;
         g.ny = p.ny;
         g.hy = p.hy;
-        g.solve = p.order == 3;
+        g.solve = solve_order(p);
     }
     tdg_status st = batch_configure(b);
     if (prev >= 0) cudaSetDevice(prev);

@@ -621,7 +621,8 @@ bool fast_side(int n) { return n == 1024 || n == 2048 || n == 4096; }
 }  // namespace
 
 bool fast_fp32_eligible(const Plan& p) {
-    return p.prec != TDG_FP64 && fast_side(p.nx) && fast_side(p.ny) && p.ax.P == 2 * p.nx && p.ay.P == 2 * p.ny;
+    return p.prec != TDG_FP64 && p.order <= 3 && fast_side(p.nx) && fast_side(p.ny) && p.ax.P == 2 * p.nx &&
+           p.ay.P == 2 * p.ny;
 }
 
 size_t fast_fp32_spec_bytes(const Plan& p) {

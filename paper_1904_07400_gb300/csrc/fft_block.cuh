@@ -141,31 +141,60 @@ __device__ void fft_lines(cpx<T>* s, const FftPlan& fp, int nl, const cpx<T>* tw
 }
 
 // ---------------------------------------------------------------------------------------
-// Truncated tridiagonal solve (1/8) (c_{i-1} + 6 c_i + c_{i+1}) = s_i, c = 0 outside
-// [0, n) (Sec. 2.3, Eqs. z_system / C_system with the isolated boundary condition).
-//
-// Exact LU of tridiag(1, 6, 1): d_0 = 6, d_i = 6 - 1/d_{i-1}, lam_i = 1/d_i; forward
-// y_i = 8 s_i - lam_{i-1} y_{i-1}, backward c_i = lam_i (y_i - c_{i+1}).  lam_i reaches its
-// limit 3 - 2 sqrt(2) to double precision within 32 steps.  Each thread takes a contiguous
-// chunk of a line; it starts its recurrence W steps early from a zero state (the error
-// decays as lam^W, below the working precision for W = 12 (float) / 24 (double)), or
-// exactly from the end of the line when that is near.
+// Truncated interpolation solves along one axis, c = 0 outside [0, n) (Sec. 2.3, Eqs.
+// z_system / C_system with the isolated boundary condition; orders 4 and 5 the same
+// condition with wider stencils): sum_d st_d c_{i+d} = s_i with st = b_k at the integers.
+// Scaled to integer matrices A c = S s:
+//   order 3: tridiag(1, 6, 1), S = 8        order 4: tridiag(1, 4, 1), S = 6
+//   order 5: pentadiag(1, 76, 230, 76, 1), S = 384
+// Tridiagonal (exact LU): d_0 = D, d_i = D - 1/d_{i-1}, lam_i = 1/d_i; forward
+// y_i = S s_i - lam_{i-1} y_{i-1}, backward c_i = lam_i (y_i - c_{i+1}).
+// Pentadiagonal (exact L D L^T, two subdiagonals l1_i, l2_i): forward
+// y_i = S s_i - l1_i y_{i-1} - l2_i y_{i-2}, backward c_i = y_i / D_i - l1_{i+1} c_{i+1}
+// - l2_{i+2} c_{i+2}.  The factors reach their limits to double precision within 32 rows.
+// Each thread takes a contiguous chunk of a line and starts each sweep W rows early from
+// a zero state, or exactly at the line's end when that is near.  The error of the early
+// start decays as rho^W with rho the recurrence's slowest root: 0.172 (order 3), 0.268
+// (order 4), 0.361 (order 5); W is chosen to put rho^W below the working precision.
 // ---------------------------------------------------------------------------------------
 
-template <typename T> struct SolveWarm;
-template <> struct SolveWarm<float> { static constexpr int W = 12; };
-template <> struct SolveWarm<double> { static constexpr int W = 24; };
-
 constexpr int kLamTable = 32;
+constexpr int kSolveTab = 3 * kLamTable;  // values of T in a solve's table
 
-// fills lam[0..31] (thread 0); caller syncs
 template <typename T>
-__device__ __forceinline__ void init_lambda(T* lam) {
-    if (threadIdx.x == 0) {
-        double d = 6.0;
+__host__ __device__ __forceinline__ int solve_warm(int order) {
+    const bool dbl = sizeof(T) == 8;
+    return order == 5 ? (dbl ? 40 : 18) : order == 4 ? (dbl ? 30 : 14) : (dbl ? 24 : 12);
+}
+
+__host__ __device__ __forceinline__ float solve_scale(int order) {
+    return order == 5 ? 384.f : order == 4 ? 6.f : 8.f;
+}
+
+// fills the per-row factors (thread 0); caller syncs.  order 3, 4: tab[i] = lam_i;
+// order 5: tab[i] = l1_i, tab[K + i] = l2_i, tab[2K + i] = 1 / D_i (K = kLamTable)
+template <typename T>
+__device__ __forceinline__ void init_solve_tables(T* tab, int order) {
+    if (threadIdx.x != 0) return;
+    if (order == 5) {
+        double Dm2 = 0.0, Dm1 = 0.0, l1m1 = 0.0;
         for (int i = 0; i < kLamTable; ++i) {
-            lam[i] = T(1.0 / d);
-            d = 6.0 - 1.0 / d;
+            const double l2 = i >= 2 ? 1.0 / Dm2 : 0.0;
+            const double l1 = i >= 1 ? (76.0 - l2 * l1m1 * Dm2) / Dm1 : 0.0;
+            const double D = 230.0 - l1 * l1 * Dm1 - l2 * l2 * Dm2;
+            tab[i] = T(l1);
+            tab[kLamTable + i] = T(l2);
+            tab[2 * kLamTable + i] = T(1.0 / D);
+            Dm2 = Dm1;
+            Dm1 = D;
+            l1m1 = l1;
+        }
+    } else {
+        const double Dg = order == 4 ? 4.0 : 6.0;
+        double d = Dg;
+        for (int i = 0; i < kLamTable; ++i) {
+            tab[i] = T(1.0 / d);
+            d = Dg - 1.0 / d;
         }
     }
 }
@@ -175,11 +204,10 @@ template <typename T> __device__ __forceinline__ cpx<T> vscale(cpx<T> a, T s) { 
 template <typename T> __device__ __forceinline__ T vzero(T*) { return T(0); }
 template <typename T> __device__ __forceinline__ cpx<T> vzero(cpx<T>*) { return mk(T(0), T(0)); }
 
-// src, dst: nl interleaved lines of n values (V = T or cpx<T>); tmp: same size scratch.
-// Result (c) in dst; src and dst may be the same array, tmp must differ from both.
+__device__ __forceinline__ int tab_row(int i) { return i < kLamTable ? i : kLamTable - 1; }
+
 template <typename T, typename V>
-__device__ void tridiag_solve_lines(const V* src, V* tmp, V* dst, int n, int nl, const T* lam) {
-    constexpr int W = SolveWarm<T>::W;
+__device__ void tridiag_lines(const V* src, V* tmp, V* dst, int n, int nl, const T* lam, int W, T S) {
     const T lamInf = lam[kLamTable - 1];
     const int tpl = blockDim.x / nl;           // threads per line
     const int line = threadIdx.x / tpl;
@@ -194,7 +222,7 @@ __device__ void tridiag_solve_lines(const V* src, V* tmp, V* dst, int n, int nl,
         V y;
         if (s0 < kLamTable) {
             s0 = 0;
-            y = vscale(src[line], T(8));
+            y = vscale(src[line], S);
         } else {
             y = vzero((V*)nullptr);
         }
@@ -202,7 +230,7 @@ __device__ void tridiag_solve_lines(const V* src, V* tmp, V* dst, int n, int nl,
         if (s0 == 0 && a == 0) tmp[line] = y;
         for (int i = start; i < b; ++i) {
             T l = (i - 1 < kLamTable) ? lam[i - 1] : lamInf;
-            V si = vscale(src[i * nl + line], T(8));
+            V si = vscale(src[i * nl + line], S);
             y = si - vscale(y, l);
             if (i >= a) tmp[i * nl + line] = y;
         }
@@ -230,6 +258,60 @@ __device__ void tridiag_solve_lines(const V* src, V* tmp, V* dst, int n, int nl,
         }
     }
     __syncthreads();
+}
+
+template <typename T, typename V>
+__device__ void pentadiag_lines(const V* src, V* tmp, V* dst, int n, int nl, const T* tab, int W, T S) {
+    const T* l1 = tab;
+    const T* l2 = tab + kLamTable;
+    const T* rD = tab + 2 * kLamTable;
+    const int tpl = blockDim.x / nl;
+    const int line = threadIdx.x / tpl;
+    const int t = threadIdx.x % tpl;
+    const int chunk = (n + tpl - 1) / tpl;
+    const int a = t * chunk;
+    const int b = min(n, a + chunk);
+    const bool active = line < nl && a < n;
+    if (active) {
+        // rows before max(s0, 0) count as zero: exact from row 0, else an early start
+        int s0 = a - W;
+        if (s0 < kLamTable) s0 = 0;
+        V y1 = vzero((V*)nullptr), y2 = y1;  // y_{i-1}, y_{i-2}
+        for (int i = s0; i < b; ++i) {
+            const int r = tab_row(i);
+            V y = vscale(src[i * nl + line], S) - vscale(y1, l1[r]) - vscale(y2, l2[r]);
+            if (i >= a) tmp[i * nl + line] = y;
+            y2 = y1;
+            y1 = y;
+        }
+    }
+    __syncthreads();
+    if (active) {
+        int e0 = b - 1 + W;
+        if (e0 >= n - 1) e0 = n - 1;  // exact: c_n = c_{n+1} = 0
+        V c1 = vzero((V*)nullptr), c2 = c1;  // c_{i+1}, c_{i+2}
+        for (int i = e0; i >= a; --i) {
+            V c = vscale(tmp[i * nl + line], rD[tab_row(i)]) - vscale(c1, l1[tab_row(i + 1)]) -
+                  vscale(c2, l2[tab_row(i + 2)]);
+            if (i < b) dst[i * nl + line] = c;
+            c2 = c1;
+            c1 = c;
+        }
+    }
+    __syncthreads();
+}
+
+// src, dst: nl interleaved lines of n values (V = T or cpx<T>); tmp: same size scratch.
+// Result (c) in dst; src and dst may be the same array, tmp must differ from both.  tab:
+// filled by init_solve_tables for the same order.
+template <typename T, typename V>
+__device__ void spline_solve_lines(const V* src, V* tmp, V* dst, int n, int nl, const T* tab, int order) {
+    const int W = solve_warm<T>(order);
+    const T S = T(solve_scale(order));
+    if (order == 5)
+        pentadiag_lines<T, V>(src, tmp, dst, n, nl, tab, W, S);
+    else
+        tridiag_lines<T, V>(src, tmp, dst, n, nl, tab, W, S);
 }
 
 }  // namespace tdg

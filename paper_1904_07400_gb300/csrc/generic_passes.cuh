@@ -57,7 +57,7 @@ __device__ void row_r2c_body(const T* __restrict__ in, int nrows, int ld, int nc
     const int M = fp.L;
     cpx<T>* cbuf = reinterpret_cast<cpx<T>*>(smem_raw);                 // (M + 1) * TR
     T* rbuf = reinterpret_cast<T*>(cbuf + (size_t)(M + 1) * TR);        // ncols * TR
-    T* lam = rbuf + (size_t)ncols * TR;                                 // kLamTable
+    T* lam = rbuf + (size_t)ncols * TR;                                 // kSolveTab
     const int r0 = bx * TR;
     const int nr = min(TR, nrows - r0);
 
@@ -66,9 +66,9 @@ __device__ void row_r2c_body(const T* __restrict__ in, int nrows, int ld, int nc
             int c = idx / ncols, j = idx % ncols;
             rbuf[j * TR + c] = (c < nr) ? in[(size_t)(r0 + c) * ld + j] : T(0);
         }
-        init_lambda(lam);
+        init_solve_tables(lam, solve);
         __syncthreads();
-        tridiag_solve_lines<T, T>(rbuf, reinterpret_cast<T*>(cbuf), rbuf, ncols, TR, lam);
+        spline_solve_lines<T, T>(rbuf, reinterpret_cast<T*>(cbuf), rbuf, ncols, TR, lam, solve);
         // pack z[n] = x[2n] + i x[2n+1], x zero beyond ncols
         for (int idx = threadIdx.x; idx < TR * M; idx += blockDim.x) {
             int c = idx % TR, n = idx / TR;
@@ -146,7 +146,7 @@ __device__ void row_c2r_body(const cpx<T>* __restrict__ in0, const cpx<T>* __res
         int ky = t * TW + w;
         if (ky < hy) cbuf[ky * TR + c] = (c < nr) ? in[tidx(it, r0 + c, ky)] : mk(T(0), T(0));
     }
-    if (solve) init_lambda(lam);
+    if (solve) init_solve_tables(lam, solve);
     __syncthreads();
 
     // Hermitian repack into Z[k], k < M; thread owns the pair (k, M - k)
@@ -184,7 +184,7 @@ __device__ void row_c2r_body(const cpx<T>* __restrict__ in0, const cpx<T>* __res
         rbuf[j * TR + c] = (j & 1) ? z.y : z.x;
     }
     __syncthreads();
-    tridiag_solve_lines<T, T>(rbuf, reinterpret_cast<T*>(cbuf), rbuf, ncols, TR, lam);
+    spline_solve_lines<T, T>(rbuf, reinterpret_cast<T*>(cbuf), rbuf, ncols, TR, lam, solve);
     for (int idx = threadIdx.x; idx < TR * ncols; idx += blockDim.x) {
         int c = idx / ncols, j = idx % ncols;
         if (c < nr) out[(size_t)(r0 + c) * ncols + j] = rbuf[j * TR + c];
@@ -202,8 +202,8 @@ __device__ __forceinline__ void load_column(cpx<T>* s, const cpx<T>* __restrict_
 
 // s holds the column in [0, nx) and zeros beyond; solves along x in place, restores zeros
 template <typename T>
-__device__ __forceinline__ void column_solve(cpx<T>* s, int nx, int P, const T* lam) {
-    tridiag_solve_lines<T, cpx<T>>(s, s + nx, s, nx, 1, lam);
+__device__ __forceinline__ void column_solve(cpx<T>* s, int nx, int P, const T* lam, int order) {
+    spline_solve_lines<T, cpx<T>>(s, s + nx, s, nx, 1, lam, order);
     for (int i = nx + threadIdx.x; i < P; i += blockDim.x) s[i] = mk(T(0), T(0));
     __syncthreads();
 }
@@ -222,9 +222,9 @@ __device__ void col_conv_body(const cpx<T>* __restrict__ z, const Tiled& t, int 
     for (int comp = 0; comp < 2; ++comp) {
         if (comp == 0 || !KEEP) {
             load_column(s, z, t, ky, nx, P);
-            if (solve) init_lambda(lam);
+            if (solve) init_solve_tables(lam, solve);
             __syncthreads();
-            if (solve) column_solve(s, nx, P, lam);
+            if (solve) column_solve(s, nx, P, lam, solve);
             fft_lines<T, EPT>(s, fp, 1, tw, 1, false);
             if (KEEP) {
 #pragma unroll

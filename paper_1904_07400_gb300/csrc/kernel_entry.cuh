@@ -32,37 +32,53 @@
 
 namespace tdg {
 
-// Polynomial pieces of the centred cardinal B-spline b_k, unit knot spacing, support
-// [-k/2, k/2]; piece p covers [lo + p, lo + p + 1) and is sum_i c[p][i] t^i.
+// Polynomial pieces of the centred cardinal B-spline b_k (k <= 5), unit knot spacing,
+// support [-k/2, k/2].  Piece p covers t in [lo + p, lo + p + 1) and is held in the local
+// variable s = t - (lo + p) in [0, 1): sum_i c[p][i] s^i (the uniform B-spline basis,
+// whose coefficients are those of (k-1)! b_k; well conditioned for every order).
 struct SplinePieces {
     int k;
     double lo;
-    double c[3][3];
+    double c[5][5];
 };
 
 TDG_HD SplinePieces spline_pieces(int k) {
-    SplinePieces s;
-    for (int p = 0; p < 3; ++p)
-        for (int i = 0; i < 3; ++i) s.c[p][i] = 0.0;
-    s.k = k;
+    SplinePieces sp;
+    for (int p = 0; p < 5; ++p)
+        for (int i = 0; i < 5; ++i) sp.c[p][i] = 0.0;
+    sp.k = k;
+    sp.lo = -0.5 * k;
+    // (k-1)! times the pieces, by power of s (zero entries omitted)
     if (k == 1) {
-        s.lo = -0.5;
-        s.c[0][0] = 1.0;
+        sp.c[0][0] = 1.0;
     } else if (k == 2) {
-        s.lo = -1.0;
-        s.c[0][0] = 1.0;  s.c[0][1] = 1.0;   // 1 + t on [-1, 0)
-        s.c[1][0] = 1.0;  s.c[1][1] = -1.0;  // 1 - t on [0, 1)
-    } else {
-        s.lo = -1.5;
-        s.c[0][0] = 1.125; s.c[0][1] = 1.5;  s.c[0][2] = 0.5;   // (t + 3/2)^2 / 2
-        s.c[1][0] = 0.75;  s.c[1][1] = 0.0;  s.c[1][2] = -1.0;  // 3/4 - t^2
-        s.c[2][0] = 1.125; s.c[2][1] = -1.5; s.c[2][2] = 0.5;   // (3/2 - t)^2 / 2
+        sp.c[0][1] = 1.0; sp.c[1][0] = 1.0; sp.c[1][1] = -1.0;
+    } else if (k == 3) {
+        sp.c[0][2] = 1.0; sp.c[1][0] = 1.0; sp.c[1][1] = 2.0; sp.c[1][2] = -2.0; sp.c[2][0] = 1.0;
+        sp.c[2][1] = -2.0; sp.c[2][2] = 1.0;
+    } else if (k == 4) {
+        sp.c[0][3] = 1.0; sp.c[1][0] = 1.0; sp.c[1][1] = 3.0; sp.c[1][2] = 3.0; sp.c[1][3] = -3.0;
+        sp.c[2][0] = 4.0; sp.c[2][2] = -6.0; sp.c[2][3] = 3.0; sp.c[3][0] = 1.0; sp.c[3][1] = -3.0;
+        sp.c[3][2] = 3.0; sp.c[3][3] = -1.0;
+    } else if (k == 5) {
+        sp.c[0][4] = 1.0; sp.c[1][0] = 1.0; sp.c[1][1] = 4.0; sp.c[1][2] = 6.0; sp.c[1][3] = 4.0;
+        sp.c[1][4] = -4.0; sp.c[2][0] = 11.0; sp.c[2][1] = 12.0; sp.c[2][2] = -6.0; sp.c[2][3] = -12.0;
+        sp.c[2][4] = 6.0; sp.c[3][0] = 11.0; sp.c[3][1] = -12.0; sp.c[3][2] = -6.0; sp.c[3][3] = 12.0;
+        sp.c[3][4] = -4.0; sp.c[4][0] = 1.0; sp.c[4][1] = -4.0; sp.c[4][2] = 6.0; sp.c[4][3] = -4.0;
+        sp.c[4][4] = 1.0;
     }
-    return s;
+    double f = 1.0;
+    for (int q = 2; q < k; ++q) f *= q;
+    for (int p = 0; p < k; ++p)
+        for (int i = 0; i < k; ++i) sp.c[p][i] /= f;
+    return sp;
 }
 
-TDG_HD double piece_eval(const SplinePieces& s, int p, double t) {
-    return s.c[p][0] + t * (s.c[p][1] + t * s.c[p][2]);
+// piece p at local coordinate s
+TDG_HD double piece_eval(const SplinePieces& sp, int p, double s) {
+    double acc = 0.0;
+    for (int i = sp.k - 1; i >= 0; --i) acc = acc * s + sp.c[p][i];
+    return acc;
 }
 
 // Gauss-Legendre rule on [-1, 1]: nodes x[i], weights w[i], i < q.
@@ -80,21 +96,21 @@ TDG_HD double kernel_f(double u, double v) {
 
 // Far field: sum over the k x k rectangles of the tensor Gauss-Legendre rule.
 TDG_HD double entry_far(int k, int m, int n, double dx, double dy, const GLRule& g) {
-    SplinePieces s = spline_pieces(k);
+    SplinePieces sp = spline_pieces(k);
     double acc = 0.0;
     for (int pu = 0; pu < k; ++pu) {
-        double cu = s.lo + pu + 0.5;
+        double cu = sp.lo + pu + 0.5;
         for (int a = 0; a < g.q; ++a) {
-            double tu = cu + 0.5 * g.x[a];
-            double wu = 0.5 * g.w[a] * piece_eval(s, pu, tu);
-            double u = (tu - m) * dx;
+            double su = 0.5 + 0.5 * g.x[a];
+            double wu = 0.5 * g.w[a] * piece_eval(sp, pu, su);
+            double u = (cu + 0.5 * g.x[a] - m) * dx;
             double inner = 0.0;
             for (int pv = 0; pv < k; ++pv) {
-                double cv = s.lo + pv + 0.5;
+                double cv = sp.lo + pv + 0.5;
                 for (int b = 0; b < g.q; ++b) {
-                    double tv = cv + 0.5 * g.x[b];
-                    double wv = 0.5 * g.w[b] * piece_eval(s, pv, tv);
-                    inner += wv * kernel_f(u, (tv - n) * dy);
+                    double sv = 0.5 + 0.5 * g.x[b];
+                    double wv = 0.5 * g.w[b] * piece_eval(sp, pv, sv);
+                    inner += wv * kernel_f(u, (cv + 0.5 * g.x[b] - n) * dy);
                 }
             }
             acc += wu * inner;
@@ -113,14 +129,14 @@ TDG_HD double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 // largest such rho solves a quadratic.  Tensor Gauss-Legendre with q nodes then converges
 // like rho^(-2q).  Returns the smallest rho over the k x k rectangles (1 = no bound).
 TDG_HD double entry_rho(int k, int m, int n, double dx, double dy) {
-    SplinePieces s = spline_pieces(k);
+    const double lo = -0.5 * k;
     const double hu = 0.5 * dx, hv = 0.5 * dy;
     double rmin = 1e300;
     for (int pu = 0; pu < k; ++pu) {
-        double cu = fabs((s.lo + pu + 0.5 - m) * dx);
+        double cu = fabs((lo + pu + 0.5 - m) * dx);
         double r1 = cu > hu ? (cu + sqrt(cu * cu - hu * hu + hv * hv)) / (hu + hv) : 1.0;
         for (int pv = 0; pv < k; ++pv) {
-            double cv = fabs((s.lo + pv + 0.5 - n) * dy);
+            double cv = fabs((lo + pv + 0.5 - n) * dy);
             double r2 = cv > hv ? (cv + sqrt(cv * cv - hv * hv + hu * hu)) / (hu + hv) : 1.0;
             double r = r1 > r2 ? r1 : r2;
             if (r < rmin) rmin = r;
@@ -146,44 +162,85 @@ TDG_HD int choose_order(double rho) {
     return 0;
 }
 
+// the piece's polynomial in u (by power of u) from its local form, s = (u - ul) / h;
+// used only for pieces with |ul| <= k h / 2 + 1 (near the origin), where expanding the
+// powers of (u - ul) loses little
+TDG_HD void piece_in_u(const SplinePieces& sp, int p, double ul, double h, double* e) {
+    for (int i = 0; i < 5; ++i) e[i] = 0.0;
+    // Horner on polynomials: acc = acc * (u - ul)/h + c_i
+    for (int i = sp.k - 1; i >= 0; --i) {
+        for (int q = 4; q >= 1; --q) e[q] = (e[q - 1] - ul * e[q]) / h;
+        e[0] = -ul * e[0] / h + sp.c[p][i];
+    }
+}
+
 // g(v) = int u r^-3 b_k(u/dx + m) du for v != 0, by parts (u r^-3 = -d/du r^-1):
-// g = int dt b_k'(t) / sqrt(((t - m) dx)^2 + v^2) = A(v) + L ln|v|, A analytic on either
-// side of v = 0.  Returns A and sets L.
-TDG_HD double near_inner(int k, int m, double dx, double v, double* L) {
+// g = int dt b_k'(t) / sqrt(((t - m) dx)^2 + v^2) = A(v) + (L0 + L2 v^2) ln|v|, A analytic
+// on either side of v = 0.  Pieces whose u-range contains 0 are integrated in closed form
+// (int u^j / r du for j <= 3: asinh, r, (u r - v^2 asinh)/2, r (u^2 - 2 v^2)/3, whose
+// asinh terms carry the ln|v|); the others are smooth in u and taken by the rule g.
+// Returns A and sets L0, L2.
+TDG_HD double near_inner(int k, int m, double dx, double v, double* L0, double* L2, const GLRule& g) {
+    *L0 = 0.0;
+    *L2 = 0.0;
     if (k == 1) {
         // b_1' = delta(t + 1/2) - delta(t - 1/2): two point evaluations, no log part
         double a0 = (-0.5 - m) * dx, a1 = (0.5 - m) * dx;
-        *L = 0.0;
         return 1.0 / sqrt(a0 * a0 + v * v) - 1.0 / sqrt(a1 * a1 + v * v);
     }
-    SplinePieces s = spline_pieces(k);
-    double A = 0.0, Lsum = 0.0;
+    SplinePieces sp = spline_pieces(k);
+    const double v2 = v * v;
+    double A = 0.0;
     for (int p = 0; p < k; ++p) {
-        // derivative piece b'(t) = d0 + d1 t; as a polynomial in u: c0 + c1 u
-        double d0 = s.c[p][1], d1 = 2.0 * s.c[p][2];
-        double c0 = d0 + d1 * m, c1 = d1 / dx;
-        double ul = (s.lo + p - m) * dx, uh = (s.lo + p + 1 - m) * dx;
-        double rl = sqrt(ul * ul + v * v), rh = sqrt(uh * uh + v * v);
-        // int du / r = asinh(u/|v|) = sgn(u) [ln(|u| + r) - ln|v|]  (u != 0); 0 at u = 0
-        double jl = (ul != 0.0) ? sgn(ul) * log(fabs(ul) + rl) : 0.0;
-        double jh = (uh != 0.0) ? sgn(uh) * log(fabs(uh) + rh) : 0.0;
-        A += c0 * (jh - jl) + c1 * (rh - rl);
-        Lsum -= c0 * (sgn(uh) - sgn(ul));
+        const double ul = (sp.lo + p - m) * dx, uh = ul + dx;
+        if (ul <= 0.0 && uh >= 0.0) {
+            // b as a polynomial in u, then b'(t) = dx sum_j q_j u^j; with dt = du / dx the
+            // piece contributes sum_j q_j int u^j / r du
+            double e[5];
+            piece_in_u(sp, p, ul, dx, e);
+            double q[4];
+            for (int j = 0; j < 4; ++j) q[j] = (j + 1) * e[j + 1];
+            double J[2][4];
+            const double us[2] = {ul, uh};
+            for (int z = 0; z < 2; ++z) {
+                const double u = us[z];
+                const double r = sqrt(u * u + v2);
+                const double j0 = (u != 0.0) ? sgn(u) * log(fabs(u) + r) : 0.0;  // asinh minus its log part
+                J[z][0] = j0;
+                J[z][1] = r;
+                J[z][2] = 0.5 * (u * r - v2 * j0);
+                J[z][3] = r * (u * u - 2.0 * v2) / 3.0;
+            }
+            for (int j = 0; j < 4; ++j) A += q[j] * (J[1][j] - J[0][j]);
+            const double ds = sgn(uh) - sgn(ul);
+            *L0 -= q[0] * ds;
+            *L2 += 0.5 * q[2] * ds;
+        } else {
+            // smooth: int b'(t) / r dt over the piece by Gauss-Legendre in s = t - (lo + p)
+            double acc = 0.0;
+            for (int a = 0; a < g.q; ++a) {
+                const double s = 0.5 + 0.5 * g.x[a];
+                double d = 0.0;
+                for (int i = sp.k - 1; i >= 1; --i) d = d * s + i * sp.c[p][i];
+                const double u = ul + s * dx;
+                acc += 0.5 * g.w[a] * d / sqrt(u * u + v2);
+            }
+            A += acc;
+        }
     }
-    *L = Lsum / dx;
-    return A / dx;
+    return A;
 }
 
 // g(v) directly, Gauss-Legendre in u on each piece (for |v| >= 2 dx, where the
 // integrand is smooth in u and the by-parts form would cancel)
 TDG_HD double direct_inner(int k, int m, double dx, double v, const GLRule& g) {
-    SplinePieces s = spline_pieces(k);
+    SplinePieces sp = spline_pieces(k);
     double acc = 0.0;
     for (int p = 0; p < k; ++p) {
-        double c = s.lo + p + 0.5;
+        double c = sp.lo + p + 0.5;
         for (int a = 0; a < g.q; ++a) {
             double t = c + 0.5 * g.x[a];
-            acc += 0.5 * g.w[a] * piece_eval(s, p, t) * kernel_f((t - m) * dx, v);
+            acc += 0.5 * g.w[a] * piece_eval(sp, p, 0.5 + 0.5 * g.x[a]) * kernel_f((t - m) * dx, v);
         }
     }
     return acc * dx;
@@ -208,16 +265,10 @@ TDG_HD double int_vlog(int i, double a, double b) {
 // is smooth and integrated by Gauss-Legendre (by-parts form for |v| < 2 dx, direct form
 // beyond).
 TDG_HD double entry_near(int k, int m, int n, double dx, double dy, const GLRule& g) {
-    SplinePieces s = spline_pieces(k);
+    SplinePieces sp = spline_pieces(k);
     double total = 0.0;
     for (int pv = 0; pv < k; ++pv) {
-        double tl = s.lo + pv, th = tl + 1.0;
-        double vl = (tl - n) * dy, vh = (th - n) * dy;
-        // the piece as a polynomial in v: b(v/dy + n) = e0 + e1 v + e2 v^2
-        double p0 = s.c[pv][0], p1 = s.c[pv][1], p2 = s.c[pv][2];
-        double e0 = p0 + p1 * n + p2 * n * n;
-        double e1 = (p1 + 2.0 * p2 * n) / dy;
-        double e2 = p2 / (dy * dy);
+        double vl = (sp.lo + pv - n) * dy, vh = vl + dy;
         double cuts[3] = {vl, vh, vh};
         int ncut = 2;
         if (vl < 0.0 && vh > 0.0) {
@@ -234,16 +285,16 @@ TDG_HD double entry_near(int k, int m, int n, double dx, double dy, const GLRule
                 bool at_zero = (sa == 0.0) || (sb == 0.0);
                 double vmax = fmax(fabs(sa), fabs(sb));
                 double c = 0.5 * (sa + sb), hw = 0.5 * (sb - sa);
-                double acc = 0.0, L = 0.0;
+                double acc = 0.0, L0 = 0.0, L2 = 0.0;
                 for (int q = 0; q < g.q; ++q) {
                     double v = c + hw * g.x[q];
-                    double poly = e0 + v * (e1 + v * e2);
+                    double poly = piece_eval(sp, pv, (v - vl) / dy);
                     double gv;
                     if (at_zero) {
-                        gv = near_inner(k, m, dx, v, &L);             // A(v) only
+                        gv = near_inner(k, m, dx, v, &L0, &L2, g);   // A(v) only
                     } else if (vmax < 2.0 * dx) {
-                        gv = near_inner(k, m, dx, v, &L);
-                        gv += L * log(fabs(v));                      // full g(v)
+                        gv = near_inner(k, m, dx, v, &L0, &L2, g);
+                        gv += (L0 + L2 * v * v) * log(fabs(v));     // full g(v)
                     } else {
                         gv = direct_inner(k, m, dx, v, g);
                     }
@@ -251,9 +302,16 @@ TDG_HD double entry_near(int k, int m, int n, double dx, double dy, const GLRule
                 }
                 total += hw * acc;
                 if (at_zero) {
-                    near_inner(k, m, dx, c, &L);  // L does not depend on v
-                    if (L != 0.0)
-                        total += L * (e0 * int_vlog(0, sa, sb) + e1 * int_vlog(1, sa, sb) + e2 * int_vlog(2, sa, sb));
+                    near_inner(k, m, dx, c, &L0, &L2, g);  // L0, L2 do not depend on v
+                    if (L0 != 0.0 || L2 != 0.0) {
+                        // the piece as a polynomial in v (it contains v = 0, so |vl| <= k dy / 2)
+                        double e[5];
+                        piece_in_u(sp, pv, vl, dy, e);
+                        double lp = 0.0;
+                        for (int i = 0; i < sp.k; ++i)
+                            lp += e[i] * (L0 * int_vlog(i, sa, sb) + L2 * int_vlog(i + 2, sa, sb));
+                        total += lp;
+                    }
                 }
             }
         }

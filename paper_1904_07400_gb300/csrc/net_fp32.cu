@@ -1236,7 +1236,8 @@ int net_fp32_length(int n) {
 }
 
 bool net_fp32_eligible(const Plan& p) {
-    return p.prec == TDG_FP32 && net_fp32_length(p.nx) == len_x(p) && net_fp32_length(p.ny) == len_y(p) &&
+    return p.prec == TDG_FP32 && p.order <= 3 && net_fp32_length(p.nx) == len_x(p) &&
+           net_fp32_length(p.ny) == len_y(p) &&
            encode_fn() != nullptr;
 }
 

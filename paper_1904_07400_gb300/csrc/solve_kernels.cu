@@ -91,10 +91,10 @@ __global__ void __launch_bounds__(kColThreads) k_cols_adj(const cpx<T>* __restri
         int e = threadIdx.x + q * blockDim.x;
         if (e < P) s[e] = acc[q];
     }
-    if (solve) init_lambda(lam);
+    if (solve) init_solve_tables(lam, solve);
     __syncthreads();
     fft_lines<T, kEPT>(s, fp, 1, tw, 1, true);
-    if (solve) column_solve(s, nx, P, lam);
+    if (solve) column_solve(s, nx, P, lam, solve);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) gout[tidx(t, i, ky)] = s[i];
 }
 
@@ -140,12 +140,12 @@ template <typename T>
 static size_t row_smem(int M, int ncols, int solve) {
     if (!solve) ncols = 0;
     constexpr int TR = RowCfg<T>::TR;
-    return (size_t)(M + 1) * TR * sizeof(cpx<T>) + (size_t)ncols * TR * sizeof(T) + kLamTable * sizeof(T);
+    return (size_t)(M + 1) * TR * sizeof(cpx<T>) + (size_t)ncols * TR * sizeof(T) + kSolveTab * sizeof(T);
 }
 
 template <typename T>
 static size_t col_smem(int P) {
-    return (size_t)P * sizeof(cpx<T>) + kLamTable * sizeof(T);
+    return (size_t)P * sizeof(cpx<T>) + kSolveTab * sizeof(T);
 }
 
 template <typename K>
@@ -206,7 +206,7 @@ cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* wo
     cpx<T>* gy = gx + n_el;
     const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
     const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
-    const int solve = p.order == 3;
+    const int solve = solve_order(p);
     mark(p, 0, s);
     cudaError_t e = rows_r2c<T>(sigma, p.nx, p.ny, p.ny, solve, p.ay.half, twy, z, t, p.hy, s);
     if (e != cudaSuccess) return e;
@@ -239,7 +239,7 @@ cudaError_t launch_adjoint(const Plan& p, const T* gxin, const T* gyin, T* gsig,
     cpx<T>* gc = zy + n_el;
     const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
     const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
-    const int solve = p.order == 3;
+    const int solve = solve_order(p);
     mark(p, 0, s);
     cudaError_t e = rows_r2c<T>(gxin, p.nx, p.ny, p.ny, 0, p.ay.half, twy, zx, t, p.hy, s);
     if (e != cudaSuccess) return e;

@@ -83,6 +83,9 @@ struct Plan {
 };
 
 // record the plan's instrumentation event i on stream s (no-op when none are set)
+// order of the interpolation solve a plan's passes run (0: none, C = sigma for k <= 2)
+inline int solve_order(const Plan& p) { return p.order >= 3 ? p.order : 0; }
+
 inline void mark(const Plan& p, int i, cudaStream_t s) {
     if (p.n_ev > i) cudaEventRecord(p.ev[i], s);
 }

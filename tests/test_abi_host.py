@@ -57,7 +57,7 @@ def test_init_validates_arguments(lib):
     assert lib.tdg_destroy(h) == 0
     bad = [
         (64, 64, 0, 0.1, 0.1, 1.0, 1, 0),      # order
-        (64, 64, 4, 0.1, 0.1, 1.0, 1, 0),
+        (64, 64, 6, 0.1, 0.1, 1.0, 1, 0),
         (0, 64, 3, 0.1, 0.1, 1.0, 1, 0),       # size
         (64, 64, 3, 0.0, 0.1, 1.0, 1, 0),      # spacing
         (64, 64, 3, 0.1, -1.0, 1.0, 1, 0),
@@ -77,6 +77,14 @@ def test_init_validates_arguments(lib):
     st, h = _init(lib, 4096, 1024, 3, 0.1, 0.1, 1.0, 2, 0)
     assert st == 0
     lib.tdg_destroy(h)
+    # orders 4 and 5 run the FP64 and FP32 forms; the tensor-core form is order 1-3 only
+    for k in (4, 5):
+        for prec in (0, 1):
+            st, h = _init(lib, 64, 48, k, 0.1, 0.1, 1.0, prec, 0)
+            assert st == 0 and h.value
+            lib.tdg_destroy(h)
+        st, h = _init(lib, 1024, 1024, k, 0.1, 0.1, 1.0, 2, 0)
+        assert st == 2 and not h.value
     assert lib.tdg_init(None, 64, 64, 3, 0.1, 0.1, 1.0, 1, 0) == 1
 
 
@@ -113,10 +121,13 @@ def test_solve_before_build_and_null_pointers(lib):
 def test_kernel_entry_host_matches_oracle_near_field(lib):
     from oracle import kernel_tables as kt
     worst = 0.0
-    for k in (1, 2, 3):
-        for ratio in (1.0, 0.5, 8.0):
-            for m in range(4):
-                for n in range(4):
+    for k in (1, 2, 3, 4, 5):
+        # orders 4, 5: square cells only (their route-I entries cost about a second each;
+        # thin cells are covered by the device-against-oracle table tests)
+        for ratio in ((1.0, 0.5, 8.0) if k <= 3 else (1.0,)):
+            nf = kt.near_field_size(k)
+            for m in range(nf):
+                for n in range(nf):
                     for comp in (0, 1):
                         got = native.kernel_entry_host(k, m, n, 1.0, ratio, comp)
                         ref = kt._near_entry(k, m, n, ratio, "xy"[comp])
@@ -124,20 +135,20 @@ def test_kernel_entry_host_matches_oracle_near_field(lib):
                             assert got == 0.0
                             continue
                         worst = max(worst, abs(got - ref) / abs(ref))
-    assert worst < 5e-15
+    assert worst < 1e-14
 
 
 def test_kernel_entry_host_matches_oracle_far_field(lib):
     from oracle import kernel_tables as kt
     rng = np.random.default_rng(0)
-    for k in (1, 2, 3):
+    for k in (1, 2, 3, 4, 5):
         for ratio in (1.0, 0.25, 3.0):
             ms = rng.integers(-300, 300, 30)
             ns = rng.integers(-300, 300, 30)
             for comp in ("x", "y"):
-                d = kt.effective_distance(ms, ns, 1.0, ratio)
+                d = kt.band_distance(k, ms, ns, 1.0, ratio)
                 for m, n, dd in zip(ms, ns, d):
-                    if max(abs(m), abs(n)) < kt.NEAR_FIELD:
+                    if max(abs(m), abs(n)) < kt.near_field_size(k):
                         continue
                     q = [q for lim, q in kt.FAR_BANDS if lim is None or dd < lim][0]
                     ref = kt.w_far_gl(k, np.array([m]), np.array([n]), 1.0, ratio, q, comp)[0]
@@ -145,12 +156,12 @@ def test_kernel_entry_host_matches_oracle_far_field(lib):
                     if ref == 0.0:
                         assert got == 0.0
                     else:
-                        assert abs(got - ref) < 1e-14 * abs(ref), (k, ratio, m, n, comp)
+                        assert abs(got - ref) < 2e-14 * abs(ref), (k, ratio, m, n, comp)
 
 
 def test_kernel_entry_host_symmetries(lib):
     e = native.kernel_entry_host
-    for k in (1, 2, 3):
+    for k in (1, 2, 3, 4, 5):
         assert e(k, 3, 5, 1.0, 1.0, 0) == -e(k, -3, 5, 1.0, 1.0, 0)
         assert e(k, 3, 5, 1.0, 1.0, 0) == e(k, 3, -5, 1.0, 1.0, 0)
         assert e(k, 3, 5, 1.0, 1.0, 1) == e(k, 5, 3, 1.0, 1.0, 0)
