@@ -223,7 +223,7 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
     // FP32 grids whose sides are multiples of 16 from 128 to 4096 cells run the transform
     // network, whose lengths are 512 .. 4096: pad to twice that length (any padded period
     // of at least 2n - 1 gives the same cropped result)
-    const bool net = prec == TDG_FP32 && order <= 3 && net_fp32_length(nx) && net_fp32_length(ny);
+    const bool net = prec == TDG_FP32 && net_fp32_length(nx) && net_fp32_length(ny);
     p.ax = make_axis(nx, net ? net_fp32_length(nx) : 0);
     p.ay = make_axis(ny, net ? net_fp32_length(ny) : 0);
     p.hy = p.ay.P / 2 + 1;

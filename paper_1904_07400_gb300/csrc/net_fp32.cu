@@ -36,54 +36,143 @@ constexpr int kTW = 2;  // tile width of the intermediates
 
 
 // ---------------------------------------------------------------------------------------
-// Spline coefficients by the truncated tridiagonal solve (1/8)(c_{i-1} + 6 c_i + c_{i+1})
-// = s_i (c = 0 outside the line), line length 16 T, thread t owning the chunk
-// [16 t, 16 t + 16) in registers.
+// Spline coefficients by the truncated interpolation solve along a line of length 16 T,
+// thread t owning the chunk [16 t, 16 t + 16) in registers (c = 0 outside the line).
+// Scaled matrices A c = S s (Sec. 2.3; orders 4 and 5 the same condition with the wider
+// stencils): order 3 tridiag(1, 6, 1), S = 8; order 4 tridiag(1, 4, 1), S = 6; order 5
+// pentadiag(1, 76, 230, 76, 1), S = 384.
 //
-// Exact LU: y_0 = 8 s_0, y_i = 8 s_i - lam_{i-1} y_{i-1}; c_{n-1} = lam_{n-1} y_{n-1},
-// c_i = lam_i (y_i - c_{i+1}), lam_i = 1 / d_i, d_0 = 6, d_i = 6 - 1 / d_{i-1}.  lam_i
-// equals its limit lam = 3 - 2 sqrt 2 to float precision from i = 6 on.
+// Tridiagonal, exact LU: y_0 = S s_0, y_i = S s_i - lam_{i-1} y_{i-1}; c_{n-1} =
+// lam_{n-1} y_{n-1}, c_i = lam_i (y_i - c_{i+1}), lam_i = 1 / d_i, d_0 = D, d_i = D -
+// 1 / d_{i-1}.  Pentadiagonal, exact L D L^T with subdiagonals l1_i, l2_i: y_i = S s_i -
+// l1_i y_{i-1} - l2_i y_{i-2}; c_i = y_i / D_i - l1_{i+1} c_{i+1} - l2_{i+2} c_{i+2}.  The
+// factors reach their limits to float precision within the first chunk (exact there).
 //
-// Each thread sweeps its chunk from zero in both directions (first chunk: exact lam_i).
+// Each thread sweeps its chunk from zero in both directions (first chunk: exact factors).
 // The true values differ from the local ones by the homogeneous solutions driven by the
-// two chunk edges: c = c_local + Y h + C g, with Y = y at the end of the previous chunk,
-// C = c at the start of the next one, h the backward sweep of (-lam)^(r+1), and
-// g_r = (-lam)^(16-r).  Y and C are the neighbours' local values (their own corrections
-// are below lam^16 = 6e-13 relative), exchanged by shuffles and, across warps, through
-// shared memory with one barrier.
+// chunk edges: tridiagonal c = c_local + Y h + C g (Y = y at the end of the previous chunk,
+// C = c at the start of the next one); pentadiagonal the same with two values per edge,
+// c = c_local + Y1 h1 + Y2 h2 + C1 g1 + C2 g2.  Y and C are the neighbours' local values
+// (their own corrections are rho^16 relative, rho the slowest root: 6e-13, 7e-10, 9e-8 for
+// orders 3, 4, 5), exchanged by shuffles and, across warps, through shared memory with one
+// barrier.
 // ---------------------------------------------------------------------------------------
-constexpr double kLamInf = 0.17157287525380990239662255158060;  // 3 - 2 sqrt 2
+template <int ORD>
+struct TriSpec;
+template <>
+struct TriSpec<3> {
+    static constexpr double D = 6.0, S = 8.0;
+};
+template <>
+struct TriSpec<4> {
+    static constexpr double D = 4.0, S = 6.0;
+};
+constexpr int kTriExact = 8;   // rows of the first chunk with their exact LU factor
+constexpr int kPentaExact = 10;
 
-__host__ __device__ constexpr double lam_exact(int i) {
-    double d = 6.0;
-    for (int k = 0; k < i; ++k) d = 6.0 - 1.0 / d;
+__host__ __device__ constexpr double tri_lam(double D, int i) {
+    double d = D;
+    for (int k = 0; k < i; ++k) d = D - 1.0 / d;
     return 1.0 / d;
 }
 
-__host__ __device__ constexpr double pow_neg_lam(int k) {
-    double r = 1.0;
-    for (int q = 0; q < k; ++q) r *= -kLamInf;
+// the tridiagonal solve's constants, folded at compile time
+struct TriTabs {
+    float h[16], g[16], lam[kTriExact], lamInf, S;
+};
+template <int ORD>
+__host__ __device__ constexpr TriTabs make_tri_tabs() {
+    TriTabs s{};
+    constexpr double D = TriSpec<ORD>::D;
+    const double li = tri_lam(D, 80);
+    double pw[18] = {};  // (-lam)^k
+    pw[0] = 1.0;
+    for (int k = 1; k < 18; ++k) pw[k] = -li * pw[k - 1];
+    // h_r: backward local sweep of e_r = (-lam)^(r+1)
+    double c = li * pw[16];
+    s.h[15] = (float)c;
+    for (int q = 14; q >= 0; --q) {
+        c = li * (pw[q + 1] - c);
+        s.h[q] = (float)c;
+    }
+    for (int r = 0; r < 16; ++r) s.g[r] = (float)pw[16 - r];
+    for (int i = 0; i < kTriExact; ++i) s.lam[i] = (float)tri_lam(D, i);
+    s.lamInf = (float)li;
+    s.S = (float)TriSpec<ORD>::S;
+    return s;
+}
+
+// exact L D L^T factors of pentadiag(1, 76, 230, 76, 1), row i
+struct PentaRow {
+    double l1, l2, D;
+};
+__host__ __device__ constexpr PentaRow penta_row(int i) {
+    double Dm2 = 0.0, Dm1 = 0.0, l1m1 = 0.0;
+    PentaRow r{0.0, 0.0, 230.0};
+    for (int k = 0; k <= i; ++k) {
+        const double l2 = k >= 2 ? 1.0 / Dm2 : 0.0;
+        const double l1 = k >= 1 ? (76.0 - l2 * l1m1 * Dm2) / Dm1 : 0.0;
+        const double D = 230.0 - l1 * l1 * Dm1 - l2 * l2 * Dm2;
+        r = PentaRow{l1, l2, D};
+        Dm2 = Dm1;
+        Dm1 = D;
+        l1m1 = l1;
+    }
     return r;
 }
 
-// h_r: backward local sweep of e_r = (-lam)^(r+1), r < 16
-__host__ __device__ constexpr double h_coef(int r) {
-    double c = kLamInf * pow_neg_lam(16);
-    for (int q = 14; q >= r; --q) c = kLamInf * (pow_neg_lam(q + 1) - c);
-    return c;
-}
-
-// the solve's constants, folded at compile time
-struct SolveTabs {
-    float h[16], g[16], lam[6];
+struct PentaTabs {
+    float h1[16], h2[16], g1[16], g2[16];
+    float l1[kPentaExact], l2[kPentaExact], rD[kPentaExact];
+    float l1i, l2i, rDi;
 };
-__host__ __device__ constexpr SolveTabs make_solve_tabs() {
-    SolveTabs s{};
-    for (int r = 0; r < 16; ++r) {
-        s.h[r] = (float)h_coef(r);
-        s.g[r] = (float)pow_neg_lam(16 - r);
+__host__ __device__ constexpr PentaTabs make_penta_tabs() {
+    PentaTabs s{};
+    const PentaRow inf = penta_row(120);
+    const double l1 = inf.l1, l2 = inf.l2, rD = 1.0 / inf.D;
+    // forward responses to the incoming y_{-1} (phi) and y_{-2} (psi)
+    double phi[16] = {}, psi[16] = {};
+    {
+        double a1 = 1.0, a2 = 0.0, b1 = 0.0, b2 = 1.0;  // (y_{r-1}, y_{r-2}) of phi and psi
+        for (int r = 0; r < 16; ++r) {
+            phi[r] = -l1 * a1 - l2 * a2;
+            psi[r] = -l1 * b1 - l2 * b2;
+            a2 = a1;
+            a1 = phi[r];
+            b2 = b1;
+            b1 = psi[r];
+        }
     }
-    for (int i = 0; i < 6; ++i) s.lam[i] = (float)lam_exact(i);
+    // backward sweeps from a zero future (h1, h2) and of a unit c_16 or c_17 (g1, g2)
+    double c1a = 0.0, c2a = 0.0, c1b = 0.0, c2b = 0.0;  // c_{r+1}, c_{r+2} of h1 / h2
+    double d1a = 1.0, d2a = 0.0, d1b = 0.0, d2b = 1.0;  // c_{r+1}, c_{r+2} of g1 / g2
+    for (int r = 15; r >= 0; --r) {
+        const double ha = phi[r] * rD - l1 * c1a - l2 * c2a;
+        const double hb = psi[r] * rD - l1 * c1b - l2 * c2b;
+        const double ga = -l1 * d1a - l2 * d2a;
+        const double gb = -l1 * d1b - l2 * d2b;
+        s.h1[r] = (float)ha;
+        s.h2[r] = (float)hb;
+        s.g1[r] = (float)ga;
+        s.g2[r] = (float)gb;
+        c2a = c1a;
+        c1a = ha;
+        c2b = c1b;
+        c1b = hb;
+        d2a = d1a;
+        d1a = ga;
+        d2b = d1b;
+        d1b = gb;
+    }
+    for (int i = 0; i < kPentaExact; ++i) {
+        const PentaRow r = penta_row(i);
+        s.l1[i] = (float)r.l1;
+        s.l2[i] = (float)r.l2;
+        s.rD[i] = (float)(1.0 / r.D);
+    }
+    s.l1i = (float)l1;
+    s.l2i = (float)l2;
+    s.rDi = (float)rD;
     return s;
 }
 
@@ -103,25 +192,25 @@ __device__ __forceinline__ cf shfl_down1(cf a) {
 }
 
 // x: the thread's chunk (in: s, out: c).  The line has 16 nact values (threads t < nact
-// own them; the others hold zeros and get zeros back).  edge: 2 * (nthreads / 32) values
+// own them; the others hold zeros and get zeros back).  edge: 4 * (nthreads / 32) values
 // of shared memory.  Called by all nthreads threads of the block (one __syncthreads).
-template <typename V>
-__device__ __forceinline__ void solve_chunk(V* x, int t, int nact, int nthreads, V* edge) {
-    constexpr SolveTabs K = make_solve_tabs();
-    const float li = (float)kLamInf;
+template <int ORD, typename V>
+__device__ __forceinline__ void solve_chunk_tri(V* x, int t, int nact, int nthreads, V* edge) {
+    constexpr TriTabs K = make_tri_tabs<ORD>();
+    const float li = K.lamInf;
     // forward sweep from zero (exact start on the first chunk)
-    x[0] = vs(x[0], 8.0f);
+    x[0] = vs(x[0], K.S);
 #pragma unroll
     for (int r = 1; r < 16; ++r) {
-        const float l = (t == 0 && r - 1 < 6) ? K.lam[r - 1] : li;
-        x[r] = vs(x[r], 8.0f) - vs(x[r - 1], l);
+        const float l = (t == 0 && r - 1 < kTriExact) ? K.lam[r - 1] : li;
+        x[r] = vs(x[r], K.S) - vs(x[r - 1], l);
     }
     const V ylast = x[15];
     // backward sweep from zero (lam_{n-1} = lam: exact on the last chunk)
     x[15] = vs(x[15], li);
 #pragma unroll
     for (int r = 14; r >= 0; --r) {
-        const float l = (t == 0 && r < 6) ? K.lam[r] : li;
+        const float l = (t == 0 && r < kTriExact) ? K.lam[r] : li;
         x[r] = vs(x[r] - x[r + 1], l);
     }
     const V cfirst = x[0];
@@ -139,6 +228,85 @@ __device__ __forceinline__ void solve_chunk(V* x, int t, int nact, int nthreads,
     const float keep = t < nact ? 1.0f : 0.0f;
 #pragma unroll
     for (int r = 0; r < 16; ++r) x[r] = vs(vfma(C, K.g[r], vfma(Y, K.h[r], x[r])), keep);
+}
+
+template <typename V>
+__device__ __forceinline__ void solve_chunk_penta(V* x, int t, int nact, int nthreads, V* edge) {
+    constexpr PentaTabs K = make_penta_tabs();
+    const bool first = t == 0;
+    // forward sweep from zero (exact factors on the first chunk)
+    x[0] = vs(x[0], 384.f);
+    x[1] = vs(x[1], 384.f) - vs(x[0], first ? K.l1[1] : K.l1i);
+#pragma unroll
+    for (int r = 2; r < 16; ++r) {
+        const bool ex = first && r < kPentaExact;
+        x[r] = vs(x[r], 384.f) - vs(x[r - 1], ex ? K.l1[r] : K.l1i) - vs(x[r - 2], ex ? K.l2[r] : K.l2i);
+    }
+    const V y1 = x[15], y2 = x[14];
+    // backward sweep from a zero future (exact on the last chunk: c_n = c_{n+1} = 0)
+    x[15] = vs(x[15], K.rDi);
+    x[14] = vs(x[14], K.rDi) - vs(x[15], K.l1i);
+#pragma unroll
+    for (int r = 13; r >= 0; --r) {
+        const bool ex = first && r + 2 < kPentaExact;
+        const float rd = (first && r < kPentaExact) ? K.rD[r] : K.rDi;
+        const float a1 = (first && r + 1 < kPentaExact) ? K.l1[r + 1] : K.l1i;
+        const float a2 = ex ? K.l2[r + 2] : K.l2i;
+        x[r] = vs(x[r], rd) - vs(x[r + 1], a1) - vs(x[r + 2], a2);
+    }
+    const V c0 = x[0], c1 = x[1];
+    // neighbours' edge values: y_15, y_14 of the previous chunk, c_0, c_1 of the next
+    const int lane = t & 31, w = t >> 5, nw = nthreads >> 5;
+    V Y1 = shfl_up1(y1), Y2 = shfl_up1(y2);
+    V N0 = shfl_down1(c0), N1 = shfl_down1(c1);
+    if (lane == 31) {
+        edge[w] = y1;
+        edge[nw + w] = y2;
+    }
+    if (lane == 0) {
+        edge[2 * nw + w] = c0;
+        edge[3 * nw + w] = c1;
+    }
+    __syncthreads();
+    if (lane == 0) {
+        Y1 = w > 0 ? edge[w - 1] : vzero(y1);
+        Y2 = w > 0 ? edge[nw + w - 1] : vzero(y1);
+    }
+    if (lane == 31) {
+        N0 = w + 1 < nw ? edge[2 * nw + w + 1] : vzero(y1);
+        N1 = w + 1 < nw ? edge[3 * nw + w + 1] : vzero(y1);
+    }
+    if (t == 0) {
+        Y1 = vzero(y1);
+        Y2 = vzero(y1);
+    }
+    const bool more = t + 1 < nact;
+    const V C1 = more ? vfma(y2, K.h2[0], vfma(y1, K.h1[0], N0)) : vzero(y1);
+    const V C2 = more ? vfma(y2, K.h2[1], vfma(y1, K.h1[1], N1)) : vzero(y1);
+    const float keep = t < nact ? 1.0f : 0.0f;
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        x[r] = vs(vfma(C2, K.g2[r], vfma(C1, K.g1[r], vfma(Y2, K.h2[r], vfma(Y1, K.h1[r], x[r])))), keep);
+}
+
+// order known at compile time (the forward kernels are instantiated per order)
+template <int ORD, typename V>
+__device__ __forceinline__ void solve_chunk_o(V* x, int t, int nact, int nthreads, V* edge) {
+    if constexpr (ORD == 5)
+        solve_chunk_penta<V>(x, t, nact, nthreads, edge);
+    else
+        solve_chunk_tri<ORD, V>(x, t, nact, nthreads, edge);
+}
+
+// order 3, 4 or 5 (uniform across the block)
+template <typename V>
+__device__ __forceinline__ void solve_chunk(V* x, int t, int nact, int nthreads, V* edge, int order) {
+    if (order == 5)
+        solve_chunk_penta<V>(x, t, nact, nthreads, edge);
+    else if (order == 4)
+        solve_chunk_tri<4, V>(x, t, nact, nthreads, edge);
+    else
+        solve_chunk_tri<3, V>(x, t, nact, nthreads, edge);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -326,9 +494,10 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // Shared memory: E = network buffer, later the row's cells for the TMA store; U = the
 // float row for the solve's transposition, later Z in padded natural order; edge.
 // ---------------------------------------------------------------------------------------
-template <int L>
+// ORD: the order of the row solve (0: none)
+template <int L, int ORD>
 __global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows(const float* __restrict__ sigma, int ny, int solve, int rowmap, int nx, const cf* __restrict__ nb,
+    k_net_rows(const float* __restrict__ sigma, int ny, int rowmap, int nx, const cf* __restrict__ nb,
                const cf* __restrict__ tw, const __grid_constant__ CUtensorMap zmap, cf* __restrict__ z) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
@@ -341,7 +510,7 @@ __global__ void __launch_bounds__(L / 16, 3)
     const net::Bases bs = net::load_bases<L>(nb, t);
     cf v[16];
     const int nact = ny >> 4;  // threads owning a 16-value chunk of the row
-    if (solve) {
+    if constexpr (ORD != 0) {
         // thread t owns s[16 t .. 16 t + 15]; past the row: zeros
         const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * ny) + 4 * t;
         float x[16];
@@ -353,7 +522,7 @@ __global__ void __launch_bounds__(L / 16, 3)
             x[4 * q + 2] = f.z;
             x[4 * q + 3] = f.w;
         }
-        solve_chunk<float>(x, t, nact, T, edge);
+        solve_chunk_o<ORD, float>(x, t, nact, T, edge);
         // chunk -> natural-strided pairs through U (float index f at f + 4 (f / 32))
         float* uf = reinterpret_cast<float*>(U);
 #pragma unroll
@@ -609,14 +778,15 @@ constexpr bool cols_twiddles_in_tmem() {
 template <int L>
 constexpr size_t cols_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16 +
+    return (size_t)(2 * BUF) * sizeof(cf) + 4 * (T / 32) * sizeof(cf) + 16 +
            (Stash<L>::kTmem ? 0 : (size_t)2 * 16 * T * sizeof(cf));
 }
 
 // column length nx <= L (a multiple of 16); Z, G_x, G_y hold nx rows
-template <int L>
+// ORD: the order of the column solve (0: none)
+template <int L, int ORD>
 __global__ void __launch_bounds__(L / 16, 2)
-    k_net_cols(const cf* __restrict__ z, int nx, int solve, const cf* __restrict__ nb, const cf* __restrict__ tw,
+    k_net_cols(const cf* __restrict__ z, int nx, const cf* __restrict__ nb, const cf* __restrict__ tw,
                const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
@@ -629,7 +799,7 @@ __global__ void __launch_bounds__(L / 16, 2)
     cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
     cf* xb = E + BUF;                         // the column (padded natural), later the even x result
     cf* edge = xb + BUF;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
+    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 4 * (T / 32));
     cf* sslots = reinterpret_cast<cf*>(tslot + 4);  // shared stash slots A, B (L = 512)
     const int t = threadIdx.x;
     if constexpr (kTm) {
@@ -649,11 +819,11 @@ __global__ void __launch_bounds__(L / 16, 2)
     const net::Bases bs = net::load_bases<L>(nb, t);
     const int nact = nx >> 4;
     cf v[16];
-    if (solve) {
+    if constexpr (ORD != 0) {
 #pragma unroll
         for (int r = 0; r < 16; ++r)  // row 16 t + r sits at r (nx / 16) + t
             v[r] = t < nact ? ld2(zc + (size_t)(r * nact + t) * kTW) : mk(0.f, 0.f);
-        solve_chunk<cf>(v, t, nact, T, edge);
+        solve_chunk_o<ORD, cf>(v, t, nact, T, edge);
 #pragma unroll
         for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = v[r];
         tmem_fence_before();
@@ -811,7 +981,7 @@ __global__ void __launch_bounds__(L / 16, 2)
     cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
     cf* xb = E + BUF;                         // stash C ([r][t]), then the solve's transposition
     cf* edge = xb + BUF;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 2 * (T / 32));
+    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 4 * (T / 32));
     cf* sslots = reinterpret_cast<cf*>(tslot + 4);
     const int t = threadIdx.x;
     if constexpr (kTm) {
@@ -921,7 +1091,7 @@ __global__ void __launch_bounds__(L / 16, 2)
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = xb[pad(16 * t + r)];
-        solve_chunk<cf>(v, t, nact, T, edge);
+        solve_chunk<cf>(v, t, nact, T, edge, solve);
         if (t < nact) {
 #pragma unroll
             for (int r = 0; r < 16; ++r) gc[(size_t)(r * nact + t) * kTW] = v[r];
@@ -944,7 +1114,7 @@ __global__ void __launch_bounds__(L / 16, 2)
 template <int L>
 constexpr size_t cols_adj_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF) * sizeof(cf) + 2 * (T / 32) * sizeof(cf) + 16 +
+    return (size_t)(2 * BUF) * sizeof(cf) + 4 * (T / 32) * sizeof(cf) + 16 +
            (Stash<L>::kTmem ? 0 : (size_t)2 * 16 * T * sizeof(cf));
 }
 
@@ -1010,7 +1180,7 @@ __global__ void __launch_bounds__(L / 16, 3)
                 x[2 * j] = o.x;
                 x[2 * j + 1] = o.y;
             }
-            solve_chunk<float>(x, t, nact, T, edge);  // its barrier: E is read before the next fwd
+            solve_chunk<float>(x, t, nact, T, edge, solve);  // its barrier: E is read before the next fwd
             if (t < nact) {
                 float4* dst = reinterpret_cast<float4*>(row) + 4 * t;
 #pragma unroll
@@ -1030,7 +1200,7 @@ __global__ void __launch_bounds__(L / 16, 3)
 
 template <int L>
 size_t inv_adj_bytes() {
-    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16 + 2 * (L / 16 / 32) * sizeof(float);
+    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16 + 4 * (L / 16 / 32) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1080,7 +1250,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <int L>
 size_t rows_bytes() {
-    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 2 * (L / 16 / 32) * sizeof(float);
+    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(float);
 }
 
 template <int L>
@@ -1095,8 +1265,8 @@ int len_y(const Plan& p) { return p.ay.P / 2; }
 const cf* bases_x(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw); }
 const cf* bases_y(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw) + len_x(p) / 8; }
 
-template <int LX, int LY>
-cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+template <int LX, int LY, int ORD>
+cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     const int hy = p.hy;
     const int ntile = (hy + kTW - 1) / kTW;
     const size_t n_el = (size_t)ntile * p.nx * kTW;
@@ -1105,7 +1275,6 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
     cf* gy = gx + n_el;
     const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
-    const int solve = p.order == 3;
     cudaError_t e;
     CUtensorMap zmap, gmap;
     if ((e = encode_tiles(&zmap, z, p.nx, ntile, 1, 0))) return e;
@@ -1115,14 +1284,14 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
 
     size_t sm = rows_bytes<LY>();
-    if ((e = set_smem(k_net_rows<LY>, sm))) return e;
+    if ((e = set_smem(k_net_rows<LY, ORD>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, solve, solve, p.nx, bases_y(p), twy, zmap, z);
+    k_net_rows<LY, ORD><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ORD != 0, p.nx, bases_y(p), twy, zmap, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_smem_bytes<LX>();
-    if ((e = set_smem(k_net_cols<LX>, sm))) return e;
-    k_net_cols<LX><<<hy, LX / 16, sm, s>>>(z, p.nx, solve, bases_x(p), twx,
+    if ((e = set_smem(k_net_cols<LX, ORD>, sm))) return e;
+    k_net_cols<LX, ORD><<<hy, LX / 16, sm, s>>>(z, p.nx, bases_x(p), twx,
                                            reinterpret_cast<const float2*>(p.spec_half), gx, gy);
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
@@ -1138,6 +1307,16 @@ cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, voi
 }
 
 template <int LX, int LY>
+cudaError_t run_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
+    switch (solve_order(p)) {
+        case 3: return run_net_o<LX, LY, 3>(p, sigma, fx, fy, work, s);
+        case 4: return run_net_o<LX, LY, 4>(p, sigma, fx, fy, work, s);
+        case 5: return run_net_o<LX, LY, 5>(p, sigma, fx, fy, work, s);
+        default: return run_net_o<LX, LY, 0>(p, sigma, fx, fy, work, s);
+    }
+}
+
+template <int LX, int LY>
 cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, float* gsig, void* work,
                         cudaStream_t s) {
     const int hy = p.hy;
@@ -1148,7 +1327,7 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     cf* g = zy + n_el;
     const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
-    const int solve = p.order == 3;
+    const int solve = solve_order(p);
     cudaError_t e;
     CUtensorMap zmx, zmy, gmap;
     if ((e = encode_tiles(&zmx, zx, p.nx, ntile, 1, 0))) return e;
@@ -1158,11 +1337,11 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
     size_t sm = rows_bytes<LY>();
-    if ((e = set_smem(k_net_rows<LY>, sm))) return e;
+    if ((e = set_smem(k_net_rows<LY, 0>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmx, zx);
+    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, p.nx, bases_y(p), twy, zmx, zx);
     if ((e = cudaGetLastError())) return e;
-    k_net_rows<LY><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmy, zy);
+    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, p.nx, bases_y(p), twy, zmy, zy);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_adj_smem_bytes<LX>();
@@ -1236,8 +1415,7 @@ int net_fp32_length(int n) {
 }
 
 bool net_fp32_eligible(const Plan& p) {
-    return p.prec == TDG_FP32 && p.order <= 3 && net_fp32_length(p.nx) == len_x(p) &&
-           net_fp32_length(p.ny) == len_y(p) &&
+    return p.prec == TDG_FP32 && net_fp32_length(p.nx) == len_x(p) && net_fp32_length(p.ny) == len_y(p) &&
            encode_fn() != nullptr;
 }
 

@@ -139,3 +139,31 @@ def test_batch_mixing_all_orders_equals_individual_solves():
         assert b.error() == 0
         for (fx, fy), (rx, ry) in zip(b.outs, ref):
             assert rel_l2_pair(to_np(fx), to_np(fy), to_np(rx), to_np(ry)) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(128, 144), (256, 192), (1024, 1008)])
+@pytest.mark.parametrize("k", [4, 5])
+def test_network_path_orders_4_5(shape, k):
+    # FP32 sides that are multiples of 16 from 128 to 4096 run the one-barrier transform
+    # network with its chunked register solves (tridiagonal for 4, pentadiagonal for 5)
+    import torch
+    nx, ny = shape
+    d = 1.0 / max(nx, ny)
+    sigma = syn.clumps(nx, ny, seed=nx + k)
+    p32 = _plan(nx, ny, k, d, d, "fp32")
+    assert p32.path() == 2
+    f32 = _solve(p32, sigma)
+    f64 = _solve(_plan(nx, ny, k, d, d, "fp64"), sigma)
+    assert rel_l2_pair(*f32, *f64) <= TOL_FP32
+    if nx * ny <= 256 * 192:
+        rx, ry = oracle_solver(nx, ny, k, d, d).forces(sigma)
+        assert rel_l2_pair(*f64, rx, ry) <= TOL_FP64
+        assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
+    # adjoint on the same path
+    rng = np.random.default_rng(k)
+    gx, gy = rng.standard_normal((nx, ny)), rng.standard_normal((nx, ny))
+    t = lambda a, p: torch.as_tensor(a, dtype=p.dtype, device=p.device)
+    p64 = _plan(nx, ny, k, d, d, "fp64")
+    a32 = to_np(p32.adjoint(t(gx, p32), t(gy, p32)))
+    a64 = to_np(p64.adjoint(t(gx, p64), t(gy, p64)))
+    assert np.linalg.norm(a32 - a64) / np.linalg.norm(a64) <= TOL_FP32
