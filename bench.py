@@ -143,8 +143,8 @@ class Clocks:
 # (FP32 network path, 4096x4096, order 3).  Valid only for the kernel sources it was taken
 # on: reported when their SHA-256 still matches, null otherwise.
 MEASURED_TRAFFIC = {
-    ("cols_conv", 2, 4096): {"bytes": 268_923_136 + 215_729_920,
-                             "sha256": "5d412d79f3e411c4f408ccb96f78a502d77bc354145ec772715856fed3cbe40c"},
+    ("cols_conv", 2, 4096): {"bytes": 268_841_472 + 216_026_112,
+                             "sha256": "8c3da722b899787d9a83273a46052ed778430985c2c00c8950ace50b65b6eee4"},
 }
 TRAFFIC_SOURCES = ("paper_1904_07400_gb300/csrc/net_fp32.cu", "paper_1904_07400_gb300/csrc/fft_net.cuh",
                    "paper_1904_07400_gb300/csrc/fft_reg.cuh")
