@@ -4,7 +4,10 @@
  *
  * What a solve computes (paper Eqs. eqnSigma, eqnF, eqnw, eqnwB):
  *   C          = B-spline coefficients of sigma at order k (Sec. 2.3: C = sigma for k = 1, 2;
- *                two truncated tridiagonal solves, Eqs. z_system and C_system, for k = 3)
+ *                two truncated tridiagonal solves, Eqs. z_system and C_system, for k = 3;
+ *                for k = 4, 5, the extension Sec. 2.3 and Sec. 4.2 call straightforward,
+ *                the same interpolation condition with the stencils (1, 4, 1)/6 and
+ *                (1, 76, 230, 76, 1)/384: truncated banded solves along y, then x)
  *   F^x_ij     = G * sum_{i'j'} C_{i'j'} w^x(i - i', j - j')
  *   F^y_ij     = G * sum_{i'j'} C_{i'j'} w^y(i - i', j - j')
  *   w^x(m, n)  = PV int int u (u^2+v^2)^(-3/2) b_k(u/dx + m) b_k(v/dy + n) du dv
@@ -58,10 +61,11 @@ typedef struct tdg_plan_s* tdg_plan;
 typedef struct tdg_batch_s* tdg_batch;
 typedef struct CUstream_st* tdg_stream;
 
-/* Create a plan for an nx x ny grid of cells dx x dy, B-spline order 1..3, constant G.
- * Allocates nothing on the device yet.  Errors: INVALID_ARG for order not in {1,2,3},
+/* Create a plan for an nx x ny grid of cells dx x dy, B-spline order 1..5, constant G.
+ * Allocates nothing on the device yet.  Errors: INVALID_ARG for order not in 1..5,
  * nx or ny < 1, dx or dy not finite and > 0, G not finite, out == NULL; UNSUPPORTED for
- * nx or ny > 4096; CUDA if `device` cannot be selected. */
+ * nx or ny > 4096, and for TDG_FP32_TC16 with order > 3 or sides other than 1024, 2048,
+ * 4096; CUDA if `device` cannot be selected. */
 tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double dy,
                     double G, tdg_precision prec, int device);
 

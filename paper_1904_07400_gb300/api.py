@@ -28,7 +28,7 @@ def _ptr(t: torch.Tensor) -> int:
 
 
 class Plan:
-    """One grid (nx x ny cells of dx x dy), B-spline order 1..3, precision form."""
+    """One grid (nx x ny cells of dx x dy), B-spline order 1..5, precision form."""
 
     def __init__(self, nx: int, ny: int, order: int, dx: float, dy: float, G: float = 1.0,
                  precision: str = "fp32", device: int | torch.device = 0, build: bool = True,
