@@ -93,6 +93,22 @@ size_t tdg_workspace_bytes(const tdg_plan p);
  * plan-owned workspace (allocated at the next solve).  Errors: INVALID_ARG. */
 tdg_status tdg_set_workspace(tdg_plan p, void* ptr, size_t bytes);
 
+/* Diagnostics of Sec. 3 on the device: the radial force F_R = (x F^x + y F^y) / R at the
+ * cell centres x_i = x0 + (i + 1/2) dx, y_j = y0 + (j + 1/2) dy (F_R = 0 where R = 0), and
+ * the error norms the paper's validation uses (Sec. 3.1), area-weighted:
+ * L1 = dx dy sum |e|, L2 = (dx dy sum e^2)^(1/2), Linf = max |e|.
+ *   fx, fy   the forces of a solve with this plan (nx*ny elements, the plan's type).
+ *   fr       output F_R (nx*ny elements) or NULL.
+ *   ref_fx   reference F^x (for instance the analytic force) or NULL; ref_fr the same for F_R.
+ *   norms    host array of 6 doubles: L1, L2, Linf of F^x - ref_fx, then of F_R - ref_fr
+ *            (zeros when ref_fr is NULL); NULL exactly when ref_fx is NULL.
+ * Sums are in FP64 with a fixed reduction order.  With norms, the call synchronises
+ * `stream` (the six values are copied to the host); without, it only enqueues.  Errors:
+ * INVALID_ARG (NULL or misaligned forces, non-finite origin, neither fr nor norms asked,
+ * norms without ref_fx or the reverse, ref_fr without ref_fx), OOM, CUDA. */
+tdg_status tdg_radial_diagnostics(tdg_plan p, const void* fx, const void* fy, double x0, double y0, void* fr,
+                                  const void* ref_fx, const void* ref_fr, double* norms, tdg_stream stream);
+
 /* sigma -> (F^x, F^y) (Eq. eqnF).  sigma, fx, fy: nx*ny elements each.  fx and fy must
  * not alias sigma or each other.  Errors: INVALID_ARG (null/misaligned), NOT_BUILT, OOM
  * (first call allocates the workspace if none was set), CUDA. */

@@ -130,6 +130,26 @@ class Plan:
         native.call("tdg_solve_adjoint", self._h, _ptr(gx), _ptr(gy), _ptr(gs), _stream_handle(self.device))
         return gs
 
+    def radial_diagnostics(self, fx: torch.Tensor, fy: torch.Tensor, x0: float, y0: float,
+                           ref_fx: torch.Tensor | None = None, ref_fr: torch.Tensor | None = None,
+                           want_fr: bool = True):
+        """F_R = (x F^x + y F^y) / R at the cell centres (x_i = x0 + (i + 1/2) dx, likewise y)
+        and, with references, the area-weighted L1, L2, Linf norms of F^x - ref_fx and
+        F_R - ref_fr (Sec. 3.1), all on the device.  Returns (F_R or None, six norms or None)."""
+        self._check(fx, "fx")
+        self._check(fy, "fy")
+        for t, name in ((ref_fx, "ref_fx"), (ref_fr, "ref_fr")):
+            if t is not None:
+                self._check(t, name)
+        fr = torch.empty_like(fx) if want_fr else None
+        norms = (ctypes.c_double * 6)() if ref_fx is not None else None
+        native.call("tdg_radial_diagnostics", self._h, _ptr(fx), _ptr(fy), float(x0), float(y0),
+                    _ptr(fr) if fr is not None else None, _ptr(ref_fx) if ref_fx is not None else None,
+                    _ptr(ref_fr) if ref_fr is not None else None,
+                    ctypes.cast(norms, ctypes.c_void_p) if norms is not None else None,
+                    _stream_handle(self.device))
+        return fr, (tuple(norms) if norms is not None else None)
+
     def kernel_tables(self):
         """FP64 quarter tables (w^x, w^y at 0 <= m < nx, 0 <= n < ny) copied to the host."""
         import numpy as np

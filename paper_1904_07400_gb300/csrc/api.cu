@@ -141,6 +141,8 @@ void free_plan_memory(Plan& p) {
     cudaFree(p.net_tw);
     cudaFree(p.wq);
     cudaFree(p.err);
+    cudaFree(p.diag);
+    p.diag = nullptr;
     if (p.work_owned) cudaFree(p.work);
     p.tw_x = p.tw_y = p.spec = p.spec_half = p.net_tw = nullptr;
     p.wq = nullptr;
@@ -408,6 +410,40 @@ tdg_status tdg_solve_forces(tdg_plan h, const void* sigma, void* fx, void* fy, t
     else
         e = launch_forward<float>(p, (const float*)sigma, (float*)fx, (float*)fy, p.work, s);
     return from_cuda(e);
+}
+
+tdg_status tdg_radial_diagnostics(tdg_plan h, const void* fx, const void* fy, double x0, double y0, void* fr,
+                                  const void* ref_fx, const void* ref_fr, double* norms, tdg_stream stream) {
+    if (!h || !fx || !fy || !aligned16(fx) || !aligned16(fy)) return TDG_ERR_INVALID_ARG;
+    if (!isfinite(x0) || !isfinite(y0)) return TDG_ERR_INVALID_ARG;
+    if ((norms != nullptr) != (ref_fx != nullptr) || (ref_fr && !ref_fx)) return TDG_ERR_INVALID_ARG;
+    if (!fr && !norms) return TDG_ERR_INVALID_ARG;
+    Plan& p = h->p;
+    DeviceGuard g(p.device);
+    if (!g.ok) return TDG_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (norms && !p.diag) {
+        e = cudaMalloc(&p.diag, (6 * (size_t)kDiagMaxBlocks + 6) * sizeof(double));
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    double* part = p.diag;
+    double* out = p.diag ? p.diag + 6 * (size_t)kDiagMaxBlocks : nullptr;
+    if (p.prec == TDG_FP64)
+        e = launch_radial<double>(p, (const double*)fx, (const double*)fy, x0, y0, (double*)fr, (const double*)ref_fx,
+                                  (const double*)ref_fr, part, out, s);
+    else
+        e = launch_radial<float>(p, (const float*)fx, (const float*)fy, x0, y0, (float*)fr, (const float*)ref_fx,
+                                 (const float*)ref_fr, part, out, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (norms) {
+        double tmp[6];
+        if ((e = cudaMemcpyAsync(tmp, out, sizeof(tmp), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return from_cuda(e);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return from_cuda(e);
+        for (int q = 0; q < 6; ++q) norms[q] = tmp[q];
+        if (!ref_fr) norms[3] = norms[4] = norms[5] = 0.0;
+    }
+    return TDG_OK;
 }
 
 tdg_status tdg_solve_adjoint(tdg_plan h, const void* gfx, const void* gfy, void* gsigma, tdg_stream stream) {

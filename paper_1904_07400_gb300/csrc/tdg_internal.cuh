@@ -78,11 +78,19 @@ struct Plan {
     size_t work_bytes;
     bool work_owned;
     int* err;              // device error word
+    double* diag;          // diagnostics: block partials and the six norms (on first use)
     int n_ev;              // 0 or 4: events recorded around the passes (instrumentation)
     cudaEvent_t ev[4];
 };
 
 // record the plan's instrumentation event i on stream s (no-op when none are set)
+// radial-force diagnostics (diagnostics.cu): at most kDiagMaxBlocks partial sums
+constexpr int kDiagMaxBlocks = 1024;
+int diag_blocks(const Plan& p);
+template <typename T>
+cudaError_t launch_radial(const Plan& p, const T* fx, const T* fy, double x0, double y0, T* fr, const T* rx,
+                          const T* rr, double* part, double* out, cudaStream_t s);
+
 // order of the interpolation solve a plan's passes run (0: none, C = sigma for k <= 2)
 inline int solve_order(const Plan& p) { return p.order >= 3 ? p.order : 0; }
 

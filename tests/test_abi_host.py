@@ -184,3 +184,21 @@ def test_build_from_tables_rejects_foreign_tables(lib):
     assert lib.tdg_build_kernel_tables_from(h, wx.ctypes.data, wy.ctypes.data, None) == 1
     assert lib.tdg_build_kernel_tables_from(h, None, wy.ctypes.data, None) == 1
     lib.tdg_destroy(h)
+
+
+def test_radial_diagnostics_argument_checks(lib):
+    # refused before any device work
+    st, h = _init(lib, 16, 16, 3, 0.1, 0.1, 1.0, 0, 0)
+    assert st == 0
+    buf = (ctypes.c_double * 4)()
+    a = ctypes.cast(buf, ctypes.c_void_p)
+    norms = (ctypes.c_double * 6)()
+    n = ctypes.cast(norms, ctypes.c_void_p)
+    f = lib.tdg_radial_diagnostics
+    assert f(h, None, a, 0.0, 0.0, a, None, None, None, None) == 1            # no F^x
+    assert f(h, a, a, float("nan"), 0.0, a, None, None, None, None) == 1      # origin
+    assert f(h, a, a, 0.0, 0.0, None, None, None, None, None) == 1            # nothing asked
+    assert f(h, a, a, 0.0, 0.0, a, None, None, n, None) == 1                  # norms, no reference
+    assert f(h, a, a, 0.0, 0.0, None, a, None, None, None) == 1               # reference, no norms
+    assert f(h, a, a, 0.0, 0.0, None, None, a, n, None) == 1                  # ref_fr without ref_fx
+    lib.tdg_destroy(h)
