@@ -93,6 +93,20 @@ size_t tdg_workspace_bytes(const tdg_plan p);
  * plan-owned workspace (allocated at the next solve).  Errors: INVALID_ARG. */
 tdg_status tdg_set_workspace(tdg_plan p, void* ptr, size_t bytes);
 
+/* The potential in the disk plane, a diagnostic beside the forces (the method itself never
+ * forms it, Sec. 1): Phi_ij = -G sum_{i'j'} C_{i'j'} w^phi(i - i', j - j') with
+ * w^phi(m, n) = int int b_k(u/dx + m) b_k(v/dy + n) (u^2 + v^2)^(-1/2) du dv (even in m and
+ * n), by the same zero-padded convolution with one real spectrum.
+ * tdg_build_potential_tables: builds w^phi in FP64 on the device and its spectrum in the
+ * plan's precision (hy x P_x values; after tdg_build_kernel_tables, whose twiddles it
+ * uses); synchronises `stream`.  Errors: NOT_BUILT, OOM, CUDA.
+ * tdg_solve_potential: sigma -> Phi (nx*ny elements each, the plan's type, 16-byte
+ * aligned, not aliased), asynchronous on `stream`, in the plan's workspace; every
+ * precision form runs the generic kernels.  Errors: INVALID_ARG, NOT_BUILT (no potential
+ * spectrum), OOM, CUDA. */
+tdg_status tdg_build_potential_tables(tdg_plan p, tdg_stream stream);
+tdg_status tdg_solve_potential(tdg_plan p, const void* sigma, void* phi, tdg_stream stream);
+
 /* Diagnostics of Sec. 3 on the device: the radial force F_R = (x F^x + y F^y) / R at the
  * cell centres x_i = x0 + (i + 1/2) dx, y_j = y0 + (j + 1/2) dy (F_R = 0 where R = 0), and
  * the error norms the paper's validation uses (Sec. 3.1), area-weighted:
@@ -189,8 +203,9 @@ tdg_status tdg_get_device_error(tdg_plan p);
  * after tdg_build_kernel_tables.  Errors: NOT_BUILT, INVALID_ARG, CUDA. */
 tdg_status tdg_copy_kernel_tables(const tdg_plan p, double* wx, double* wy);
 
-/* Evaluate one kernel-table entry w^x(m, n) (component 0) or w^y(m, n) (component 1) on
- * the HOST with the same FP64 code the device build runs.  For tests without a GPU.
+/* Evaluate one kernel-table entry w^x(m, n) (component 0), w^y(m, n) (component 1) or the
+ * potential kernel w^phi(m, n) (component 2, see tdg_build_potential_tables) on the HOST
+ * with the same FP64 code the device build runs.  For tests without a GPU.
  * Errors: INVALID_ARG for bad order/spacing/component or out == NULL. */
 tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy,
                                  int component, double* out);

@@ -116,3 +116,22 @@ def cartesian_force(n: int, x, y, a: float, sigma0: float = 1.0, G: float = 1.0)
     R = np.hypot(x, y)
     fr = radial_force(n, R, a, sigma0, G)
     return fr * x / R, fr * y / R, fr
+
+
+def disk_potential(n: int, R, a: float, sigma0: float = 1.0, G: float = 1.0, dps: int = 25):
+    """Potential of the D_n disk in its plane, Phi(R) = -G int sigma(R') R' dR' dphi / |x - x'|,
+    by quadrature: the angular integral is 4 K(k^2) / (R + R'), k^2 = 4 R R' / (R + R')^2,
+    with K from the arithmetic-geometric mean, K = pi / (2 agm(1, |R - R'| / (R + R'))).
+    D_1 inside the disk has the closed form -(pi^2 G sigma_0 / (4 a)) (2 a^2 - R^2) (tests)."""
+    R = np.atleast_1d(np.asarray(R, dtype=np.float64))
+    out = np.empty_like(R)
+    with mp.workdps(dps):
+        for i, Rv in enumerate(R):
+            Rm = mp.mpf(Rv)
+
+            def f(Rp):
+                return (1 - Rp * Rp / (a * a)) ** (n - mp.mpf(1) / 2) * Rp / (Rm + Rp) \
+                    * mp.pi / (2 * mp.agm(1, abs(Rm - Rp) / (Rm + Rp)))
+            pts = [0, Rm, a] if Rv < a else [0, a]
+            out[i] = float(-4 * G * sigma0 * mp.quad(f, pts))
+    return out

@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 from .coefficients import adjoint_coefficients, bspline_coefficients
-from .kernel_tables import kernel_tables
+from .kernel_tables import kernel_tables, potential_table
 
 
 def forces_direct(c: np.ndarray, wx: np.ndarray, wy: np.ndarray, G: float = 1.0):
@@ -93,6 +93,26 @@ def correlate_direct(gx, gy, wx, wy, G: float = 1.0):
     return G * out
 
 
+def potential_direct(c: np.ndarray, wphi: np.ndarray, G: float = 1.0):
+    """Phi_ij = -G sum_{i'j'} C_{i'j'} w^phi(i - i', j - j') as a literal double sum."""
+    nx, ny = c.shape
+    out = np.zeros((nx, ny))
+    for i in range(nx):
+        for j in range(ny):
+            rows = slice(i + nx - 1, i - 1 if i > 0 else None, -1)
+            cols = slice(j + ny - 1, j - 1 if j > 0 else None, -1)
+            out[i, j] = np.sum(c * wphi[rows, cols])
+    return -G * out
+
+
+def potential_fft(c: np.ndarray, wphi: np.ndarray, G: float = 1.0):
+    """The same through zero-padded FFTs (one forward transform of C, one inverse)."""
+    nx, ny = c.shape
+    px, py = 2 * nx, 2 * ny
+    spec = np.fft.rfft2(place_periodic(wphi, px, py))
+    return -G * np.fft.irfft2(np.fft.rfft2(c, s=(px, py)) * spec, s=(px, py))[:nx, :ny]
+
+
 class Solver:
     """The oracle's whole force solve for one grid: tables once, then sigma -> forces.
 
@@ -131,6 +151,15 @@ class Solver:
             fx.append(self.G * np.sum(c * self.wx[rows, cols]))
             fy.append(self.G * np.sum(c * self.wy[rows, cols]))
         return np.array(fx), np.array(fy)
+
+    def potential(self, sigma, method: str = "fft"):
+        """Phi at the cell centres (the potential kernel's table is built on first use)."""
+        if getattr(self, "_wphi", None) is None:
+            self._wphi = potential_table(self.k, self.nx, self.ny, self.dx, self.dy)
+        c = self.coefficients(sigma)
+        if method == "direct":
+            return potential_direct(c, self._wphi, self.G)
+        return potential_fft(c, self._wphi, self.G)
 
     def adjoint(self, gx, gy, method: str = "fft"):
         """dL/dsigma for L = sum(gx F^x + gy F^y)."""

@@ -395,3 +395,122 @@ def _unfold(q: np.ndarray, odd_axis: int) -> np.ndarray:
     else:
         full[:, ny - 1] = 0.0
     return full
+
+
+# ----------------------------------------------------------------------------------
+# Potential kernel (a diagnostic beside the forces; the paper itself never forms the
+# potential, Sec. 1): Phi_ij = -G sum C_{i'j'} w^phi(i - i', j - j') with
+#     w^phi(m, n) = int int b_k(u/dx + m) b_k(v/dy + n) (u^2 + v^2)^(-1/2) du dv,
+# even in m and n, absolutely convergent (1/r is integrable in 2-D), and proportional to
+# the cell size (w^phi(m, n; s dx, s dy) = s w^phi(m, n; dx, dy)).
+# ----------------------------------------------------------------------------------
+
+
+def _inner_phi(k: int, m: int, h: float, v):
+    """int b_k(u/h + m) / sqrt(u^2 + v^2) du, v != 0: closed form on each piece."""
+    total = mp.mpf(0)
+    for lo, hi, cs in pieces_exact(k):
+        q = _compose(cs, m, h)  # b(u/h + m) as a polynomial in u
+        ul, uh = (_mpf(lo) - m) * mp.mpf(h), (_mpf(hi) - m) * mp.mpf(h)
+        for j, c in enumerate(q):
+            if c != 0:
+                total += c * (_J(j, uh, v) - _J(j, ul, v))
+    return total
+
+
+def w_phi_route(k: int, m: int, n: int, dx: float, dy: float, dps: int = 30):
+    """w^phi at one offset: the u-integral in closed form, then an mpmath quadrature in v
+    split at v = 0 (a logarithmic endpoint singularity) and at the knots."""
+    with mp.workdps(dps):
+        total = mp.mpf(0)
+        for lo, hi, cs in pieces_exact(k):
+            vl, vh = (_mpf(lo) - n) * mp.mpf(dy), (_mpf(hi) - n) * mp.mpf(dy)
+            pts = [vl, vh]
+            if vl < 0 < vh:
+                pts = [vl, mp.mpf(0), vh]
+            pv = _MPoly(_compose(cs, n, dy))
+
+            def f(v, pv=pv):
+                return _poly_mp(pv, v) * _inner_phi(k, m, dx, v)
+
+            total += mp.quad(f, pts)
+        return total
+
+
+def w_phi_k1_closed(m: int, n: int, dx: float, dy: float):
+    """Order 1 in closed form: the potential integral of a uniform rectangle, with the
+    textbook antiderivative of 1/r, u ln(v + r) + v ln(u + r), written as
+    A(u, v) = u asinh(v/|u|) + v asinh(u/|v|) (the two differ by functions of u alone and
+    of v alone, which cancel at the four corners; A's terms vanish on the axes)."""
+    with mp.workdps(40):
+        def A(u, v):
+            u, v = mp.mpf(u), mp.mpf(v)
+            a = u * mp.asinh(v / abs(u)) if u != 0 else mp.mpf(0)
+            b = v * mp.asinh(u / abs(v)) if v != 0 else mp.mpf(0)
+            return a + b
+        ul, uh = (-0.5 - m) * dx, (0.5 - m) * dx
+        vl, vh = (-0.5 - n) * dy, (0.5 - n) * dy
+        return A(uh, vh) - A(ul, vh) - A(uh, vl) + A(ul, vl)
+
+
+def w_phi_far_gl(k: int, ms: np.ndarray, ns: np.ndarray, dx: float, dy: float, q: int) -> np.ndarray:
+    """sum_a sum_b W_a W_b / r((t_a - m) dx, (t_b - n) dy) dx dy for arrays of offsets."""
+    ms = np.asarray(ms, dtype=np.float64)
+    ns = np.asarray(ns, dtype=np.float64)
+    t, wt = _gl_nodes(k, q)
+    out = np.zeros(np.broadcast(ms, ns).shape)
+    for ta, wa in zip(t, wt):
+        u = (ta - ms) * dx
+        for tb, wb in zip(t, wt):
+            v = (tb - ns) * dy
+            out += (wa * wb) / np.sqrt(u * u + v * v)
+    return out * dx * dy
+
+
+@functools.lru_cache(maxsize=None)
+def _near_phi(k: int, m: int, n: int, ratio: float) -> float:
+    # unit dx; scaled by dx by the caller.  Square cells: symmetric in (m, n)
+    if ratio == 1.0 and n < m:
+        return _near_phi(k, n, m, ratio)
+    return float(w_phi_route(k, m, n, 1.0, ratio, dps=20))
+
+
+def potential_table_quarter(k: int, nx: int, ny: int, dx: float, dy: float, chunk: int = 256) -> np.ndarray:
+    """w^phi at offsets 0 <= m < nx, 0 <= n < ny (even in both), assembled like the force
+    tables: near field by the closed-form inner integral and quadrature, far field by the
+    Gauss-Legendre bands."""
+    out = np.zeros((nx, ny))
+    nf = near_field_size(k)
+    for m in range(min(nx, nf)):
+        for n in range(min(ny, nf)):
+            out[m, n] = dx * _near_phi(k, m, n, dy / dx)
+    for m0 in range(0, nx, chunk):
+        mm = np.arange(m0, min(nx, m0 + chunk))[:, None]
+        nn = np.arange(ny)[None, :]
+        d = band_distance(k, mm, nn, dx, dy)
+        near = np.maximum(mm, nn) < nf
+        block = np.zeros(d.shape)
+        lower = 0.0
+        for limit, q in FAR_BANDS:
+            upper = np.inf if limit is None else limit
+            sel = (d >= lower) & (d < upper) & ~near
+            if sel.any():
+                mi, ni = np.nonzero(sel)
+                block[mi, ni] = w_phi_far_gl(k, mm[mi, 0], nn[0, ni], dx, dy, q)
+            if limit is None:
+                break
+            lower = limit
+        block[near] = out[m0:m0 + chunk][near]
+        out[m0:m0 + chunk] = block
+    return out
+
+
+def potential_table(k: int, nx: int, ny: int, dx: float, dy: float) -> np.ndarray:
+    """Full table of shape (2nx-1, 2ny-1), index [m + nx - 1, n + ny - 1]."""
+    q = potential_table_quarter(k, nx, ny, dx, dy)
+    full = np.zeros((2 * nx - 1, 2 * ny - 1))
+    full[nx - 1:, ny - 1:] = q
+    full[:nx - 1, ny - 1:] = q[:0:-1, :]
+    full[nx - 1:, :ny - 1] = q[:, :0:-1]
+    full[:nx - 1, :ny - 1] = q[:0:-1, :0:-1]
+    return full

@@ -130,6 +130,19 @@ class Plan:
         native.call("tdg_solve_adjoint", self._h, _ptr(gx), _ptr(gy), _ptr(gs), _stream_handle(self.device))
         return gs
 
+    def build_potential(self) -> None:
+        """Build the potential kernel's table and spectrum (after the force tables)."""
+        with torch.cuda.device(self.device):
+            native.call("tdg_build_potential_tables", self._h, _stream_handle(self.device))
+
+    def potential(self, sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Phi = -G sum C w^phi at the cell centres (build_potential first)."""
+        self._check(sigma, "sigma")
+        phi = torch.empty_like(sigma) if out is None else out
+        self._check(phi, "phi")
+        native.call("tdg_solve_potential", self._h, _ptr(sigma), _ptr(phi), _stream_handle(self.device))
+        return phi
+
     def radial_diagnostics(self, fx: torch.Tensor, fy: torch.Tensor, x0: float, y0: float,
                            ref_fx: torch.Tensor | None = None, ref_fr: torch.Tensor | None = None,
                            want_fr: bool = True):

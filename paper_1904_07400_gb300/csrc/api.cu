@@ -143,6 +143,8 @@ void free_plan_memory(Plan& p) {
     cudaFree(p.err);
     cudaFree(p.diag);
     p.diag = nullptr;
+    cudaFree(p.spec_phi);
+    p.spec_phi = nullptr;
     if (p.work_owned) cudaFree(p.work);
     p.tw_x = p.tw_y = p.spec = p.spec_half = p.net_tw = nullptr;
     p.wq = nullptr;
@@ -412,6 +414,75 @@ tdg_status tdg_solve_forces(tdg_plan h, const void* sigma, void* fx, void* fy, t
     return from_cuda(e);
 }
 
+tdg_status tdg_build_potential_tables(tdg_plan h, tdg_stream stream) {
+    if (!h) return TDG_ERR_INVALID_ARG;
+    Plan& p = h->p;
+    if (!p.built) return TDG_ERR_NOT_BUILT;
+    DeviceGuard g(p.device);
+    if (!g.ok) return TDG_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int Px = p.ax.P, Py = p.ay.P;
+    const HostRules& R = host_rules();
+    const size_t ntile64 = (size_t)(p.hy + 1) / 2;
+    const size_t scratch_bytes = (ntile64 * Px * 2 + Px + Py) * sizeof(cpx<double>);
+    double *placed = nullptr, *glx = nullptr, *glw = nullptr;
+    void* scratch = nullptr;
+    cudaFree(p.spec_phi);
+    p.spec_phi = nullptr;
+    cudaError_t e;
+#define TDG_TRY(call)              \
+    do {                           \
+        e = (call);                \
+        if (e != cudaSuccess) goto fail; \
+    } while (0)
+    TDG_TRY(cudaMalloc(&p.spec_phi, (size_t)p.hy * Px * p.elem));
+    TDG_TRY(cudaMalloc(&placed, (size_t)Px * Py * sizeof(double)));
+    TDG_TRY(cudaMalloc(&scratch, scratch_bytes));
+    TDG_TRY(cudaMalloc(&glx, R.x.size() * sizeof(double)));
+    TDG_TRY(cudaMalloc(&glw, R.w.size() * sizeof(double)));
+    TDG_TRY(cudaMemcpyAsync(glx, R.x.data(), R.x.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TDG_TRY(cudaMemcpyAsync(glw, R.w.data(), R.w.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TDG_TRY(cudaMemsetAsync(placed, 0, (size_t)Px * Py * sizeof(double), s));
+    TDG_TRY(launch_build_phi_table(p, placed, glx, glw, s));
+    if (p.prec == TDG_FP64)
+        TDG_TRY(launch_potential_spectrum<double>(p, placed, scratch, reinterpret_cast<double*>(p.spec_phi), s));
+    else
+        TDG_TRY(launch_potential_spectrum<float>(p, placed, scratch, reinterpret_cast<float*>(p.spec_phi), s));
+    TDG_TRY(cudaStreamSynchronize(s));
+    cudaFree(placed);
+    cudaFree(scratch);
+    cudaFree(glx);
+    cudaFree(glw);
+    return TDG_OK;
+fail:
+    cudaStreamSynchronize(s);
+    cudaFree(placed);
+    cudaFree(scratch);
+    cudaFree(glx);
+    cudaFree(glw);
+    cudaFree(p.spec_phi);
+    p.spec_phi = nullptr;
+    return from_cuda(e);
+#undef TDG_TRY
+}
+
+tdg_status tdg_solve_potential(tdg_plan h, const void* sigma, void* phi, tdg_stream stream) {
+    if (!h || !sigma || !phi || !aligned16(sigma) || !aligned16(phi) || sigma == phi) return TDG_ERR_INVALID_ARG;
+    Plan& p = h->p;
+    if (!p.built || !p.spec_phi) return TDG_ERR_NOT_BUILT;
+    DeviceGuard g(p.device);
+    if (!g.ok) return TDG_ERR_CUDA;
+    tdg_status st = ensure_workspace(p);
+    if (st != TDG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (p.prec == TDG_FP64)
+        e = launch_potential<double>(p, (const double*)sigma, (double*)phi, p.work, s);
+    else
+        e = launch_potential<float>(p, (const float*)sigma, (float*)phi, p.work, s);
+    return from_cuda(e);
+}
+
 tdg_status tdg_radial_diagnostics(tdg_plan h, const void* fx, const void* fy, double x0, double y0, void* fr,
                                   const void* ref_fx, const void* ref_fr, double* norms, tdg_stream stream) {
     if (!h || !fx || !fy || !aligned16(fx) || !aligned16(fy)) return TDG_ERR_INVALID_ARG;
@@ -499,8 +570,12 @@ tdg_status tdg_copy_kernel_tables(const tdg_plan h, double* wx, double* wy) {
 }
 
 tdg_status tdg_kernel_entry_host(int order, int m, int n, double dx, double dy, int component, double* out) {
-    if (!out || order < 1 || order > 5 || component < 0 || component > 1) return TDG_ERR_INVALID_ARG;
+    if (!out || order < 1 || order > 5 || component < 0 || component > 2) return TDG_ERR_INVALID_ARG;
     if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy)) return TDG_ERR_INVALID_ARG;
+    if (component == 2) {  // the potential kernel, even in m and n
+        *out = entry_phi(order, m < 0 ? -m : m, n < 0 ? -n : n, dx, dy, host_rules().rules);
+        return TDG_OK;
+    }
     if (component == 1) {  // w^y(m, n; dx, dy) = w^x(n, m; dy, dx)
         int t = m;
         m = n;

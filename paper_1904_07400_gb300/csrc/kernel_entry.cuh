@@ -330,4 +330,156 @@ TDG_HD double entry_x(int k, int m, int n, double dx, double dy, const GLRule* r
     return entry_far(k, m, n, dx, dy, rules[i]);
 }
 
+// ---------------------------------------------------------------------------------------
+// Potential kernel (a diagnostic beside the forces; Sec. 1 notes that the method never
+// forms the potential): w^phi(m, n) = int int b_k(u/dx + m) b_k(v/dy + n) / r du dv, even in
+// m and n and absolutely convergent.  Same structure as the force entries:
+//  * far field: tensor Gauss-Legendre with 1/r (same rectangles and node counts);
+//  * near field: w = int dv b_k(v/dy + n) h(v), h(v) = int b_k(u/dx + m) / r du =
+//    A(v) + (L0 + L2 v^2 + L4 v^4) ln|v|; the piece whose u-range contains 0 in closed form
+//    (int u^j / r du, j <= 4: asinh, r, (u r - v^2 asinh)/2, r (u^2 - 2 v^2)/3,
+//    u^3 r / 4 - (3/4) v^2 J_2), the others by Gauss-Legendre.
+// ---------------------------------------------------------------------------------------
+TDG_HD double phi_far(int k, int m, int n, double dx, double dy, const GLRule& g) {
+    SplinePieces sp = spline_pieces(k);
+    double acc = 0.0;
+    for (int pu = 0; pu < k; ++pu) {
+        double cu = sp.lo + pu + 0.5;
+        for (int a = 0; a < g.q; ++a) {
+            double wu = 0.5 * g.w[a] * piece_eval(sp, pu, 0.5 + 0.5 * g.x[a]);
+            double u = (cu + 0.5 * g.x[a] - m) * dx;
+            double inner = 0.0;
+            for (int pv = 0; pv < k; ++pv) {
+                double cv = sp.lo + pv + 0.5;
+                for (int b = 0; b < g.q; ++b) {
+                    double wv = 0.5 * g.w[b] * piece_eval(sp, pv, 0.5 + 0.5 * g.x[b]);
+                    double v = (cv + 0.5 * g.x[b] - n) * dy;
+                    inner += wv / sqrt(u * u + v * v);
+                }
+            }
+            acc += wu * inner;
+        }
+    }
+    return acc * dx * dy;
+}
+
+// h(v) for |v| < 2 dx: returns A(v), sets L0, L2, L4
+TDG_HD double phi_inner_near(int k, int m, double dx, double v, double* L0, double* L2, double* L4, const GLRule& g) {
+    SplinePieces sp = spline_pieces(k);
+    const double v2 = v * v;
+    double A = 0.0;
+    *L0 = *L2 = *L4 = 0.0;
+    for (int p = 0; p < k; ++p) {
+        const double ul = (sp.lo + p - m) * dx, uh = ul + dx;
+        if (ul <= 0.0 && uh >= 0.0) {
+            double e[5];
+            piece_in_u(sp, p, ul, dx, e);  // b(u/dx + m) = sum_j e_j u^j on the piece
+            double J[2][5];
+            const double us[2] = {ul, uh};
+            for (int z = 0; z < 2; ++z) {
+                const double u = us[z];
+                const double r = sqrt(u * u + v2);
+                const double j0 = (u != 0.0) ? sgn(u) * log(fabs(u) + r) : 0.0;
+                J[z][0] = j0;
+                J[z][1] = r;
+                J[z][2] = 0.5 * (u * r - v2 * j0);
+                J[z][3] = r * (u * u - 2.0 * v2) / 3.0;
+                J[z][4] = 0.25 * u * u * u * r - 0.75 * v2 * J[z][2];
+            }
+            for (int j = 0; j < 5; ++j) A += e[j] * (J[1][j] - J[0][j]);
+            const double ds = sgn(uh) - sgn(ul);
+            *L0 -= e[0] * ds;
+            *L2 += 0.5 * e[2] * ds;
+            *L4 -= 0.375 * e[4] * ds;
+        } else {
+            double acc = 0.0;
+            for (int a = 0; a < g.q; ++a) {
+                const double s = 0.5 + 0.5 * g.x[a];
+                const double u = ul + s * dx;
+                acc += 0.5 * g.w[a] * piece_eval(sp, p, s) / sqrt(u * u + v2);
+            }
+            A += acc * dx;
+        }
+    }
+    return A;
+}
+
+TDG_HD double phi_inner_direct(int k, int m, double dx, double v, const GLRule& g) {
+    SplinePieces sp = spline_pieces(k);
+    double acc = 0.0;
+    for (int p = 0; p < k; ++p) {
+        for (int a = 0; a < g.q; ++a) {
+            const double s = 0.5 + 0.5 * g.x[a];
+            const double u = (sp.lo + p + s - m) * dx;
+            acc += 0.5 * g.w[a] * piece_eval(sp, p, s) / sqrt(u * u + v * v);
+        }
+    }
+    return acc * dx;
+}
+
+TDG_HD double phi_near(int k, int m, int n, double dx, double dy, const GLRule& g) {
+    SplinePieces sp = spline_pieces(k);
+    double total = 0.0;
+    for (int pv = 0; pv < k; ++pv) {
+        double vl = (sp.lo + pv - n) * dy, vh = vl + dy;
+        double cuts[3] = {vl, vh, vh};
+        int ncut = 2;
+        if (vl < 0.0 && vh > 0.0) {
+            cuts[1] = 0.0;
+            ncut = 3;
+        }
+        for (int h = 0; h + 1 < ncut; ++h) {
+            double a = cuts[h], b = cuts[h + 1];
+            int nsub = (int)ceil(2.0 * (b - a) / dx);
+            if (nsub < 1) nsub = 1;
+            double width = (b - a) / nsub;
+            for (int si = 0; si < nsub; ++si) {
+                double sa = a + si * width, sb = (si == nsub - 1) ? b : sa + width;
+                bool at_zero = (sa == 0.0) || (sb == 0.0);
+                double vmax = fmax(fabs(sa), fabs(sb));
+                double c = 0.5 * (sa + sb), hw = 0.5 * (sb - sa);
+                double acc = 0.0, L0 = 0.0, L2 = 0.0, L4 = 0.0;
+                for (int q = 0; q < g.q; ++q) {
+                    double v = c + hw * g.x[q];
+                    double poly = piece_eval(sp, pv, (v - vl) / dy);
+                    double hv;
+                    if (at_zero) {
+                        hv = phi_inner_near(k, m, dx, v, &L0, &L2, &L4, g);
+                    } else if (vmax < 2.0 * dx) {
+                        hv = phi_inner_near(k, m, dx, v, &L0, &L2, &L4, g);
+                        const double v2 = v * v;
+                        hv += (L0 + v2 * (L2 + v2 * L4)) * log(fabs(v));
+                    } else {
+                        hv = phi_inner_direct(k, m, dx, v, g);
+                    }
+                    acc += g.w[q] * poly * hv;
+                }
+                total += hw * acc;
+                if (at_zero) {
+                    phi_inner_near(k, m, dx, c, &L0, &L2, &L4, g);  // L0, L2, L4 do not depend on v
+                    if (L0 != 0.0 || L2 != 0.0 || L4 != 0.0) {
+                        double e[5];
+                        piece_in_u(sp, pv, vl, dy, e);
+                        double lp = 0.0;
+                        for (int i = 0; i < sp.k; ++i)
+                            lp += e[i] * (L0 * int_vlog(i, sa, sb) + L2 * int_vlog(i + 2, sa, sb) +
+                                          L4 * int_vlog(i + 4, sa, sb));
+                        total += lp;
+                    }
+                }
+            }
+        }
+    }
+    return total;
+}
+
+// One potential-table entry w^phi(m, n), m, n >= 0
+TDG_HD double entry_phi(int k, int m, int n, double dx, double dy, const GLRule* rules) {
+    int q = choose_order(entry_rho(k, m, n, dx, dy));
+    if (q == 0) return phi_near(k, m, n, dx, dy, rules[kNearRule]);
+    int i = 0;
+    while (rule_order(i) != q) ++i;
+    return phi_far(k, m, n, dx, dy, rules[i]);
+}
+
 }  // namespace tdg

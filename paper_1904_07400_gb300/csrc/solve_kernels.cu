@@ -99,11 +99,12 @@ __global__ void __launch_bounds__(kColThreads) k_cols_adj(const cpx<T>* __restri
 }
 
 // Spectrum of the placed tables: column FFT of the row-transformed tables, keep the
-// imaginary part (the tables are odd along the force axis) scaled by G / (P_x P_y).
+// imaginary part (force tables: odd along the force axis) or the real part (potential
+// table: even in both), times the scale (G or -G over P_x P_y).
 template <typename T>
 __global__ void __launch_bounds__(kColThreads) k_cols_spectrum(const cpx<double>* __restrict__ z, Tiled t, int hy,
                                                         FftPlan fp, const cpx<double>* __restrict__ tw,
-                                                        double scale, T* __restrict__ spec) {
+                                                        double scale, int real_part, T* __restrict__ spec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = fp.L;
     cpx<double>* s = reinterpret_cast<cpx<double>*>(smem_raw);
@@ -111,7 +112,31 @@ __global__ void __launch_bounds__(kColThreads) k_cols_spectrum(const cpx<double>
     for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = z[tidx(t, i, ky)];
     __syncthreads();
     fft_lines<double, kEPT>(s, fp, 1, tw, 1, false);
-    for (int e = threadIdx.x; e < P; e += blockDim.x) spec[(size_t)ky * P + e] = T(scale * s[e].y);
+    for (int e = threadIdx.x; e < P; e += blockDim.x)
+        spec[(size_t)ky * P + e] = T(scale * (real_part ? s[e].x : s[e].y));
+}
+
+// Pass B of the potential: column ky of Z, x solve, transform, times the real potential
+// spectrum, inverse transform, crop
+template <typename T>
+__global__ void __launch_bounds__(kColThreads) k_cols_pot(const cpx<T>* __restrict__ z, Tiled t, int nx, int hy,
+                                                   int solve, FftPlan fp, const cpx<T>* __restrict__ tw,
+                                                   const T* __restrict__ spec, cpx<T>* __restrict__ g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = fp.L;
+    cpx<T>* s = reinterpret_cast<cpx<T>*>(smem_raw);
+    T* lam = reinterpret_cast<T*>(s + P);
+    const int ky = blockIdx.x;
+    load_column(s, z, t, ky, nx, P);
+    if (solve) init_solve_tables(lam, solve);
+    __syncthreads();
+    if (solve) column_solve(s, nx, P, lam, solve);
+    fft_lines<T, kEPT>(s, fp, 1, tw, 1, false);
+    const T* sc = spec + (size_t)ky * P;
+    for (int e = threadIdx.x; e < P; e += blockDim.x) s[e] = scl(s[e], __ldg(sc + e));
+    __syncthreads();
+    fft_lines<T, kEPT>(s, fp, 1, tw, 1, true);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) g[tidx(t, i, ky)] = s[i];
 }
 
 template <typename T>
@@ -282,13 +307,58 @@ cudaError_t launch_spectra(const Plan& p, const double* placed_x, const double* 
         const double* placed = comp ? placed_y : placed_x;
         e = rows_r2c<double>(placed, Px, Py, Py, 0, p.ay.half, tw64y, z, t, p.hy, s);
         if (e != cudaSuccess) return e;
-        k_cols_spectrum<T><<<p.hy, nt, sm, s>>>(z, t, p.hy, p.ax.full, tw64x, scale,
+        k_cols_spectrum<T><<<p.hy, nt, sm, s>>>(z, t, p.hy, p.ax.full, tw64x, scale, 0,
                                                 spec + (size_t)comp * p.hy * Px);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+template <typename T>
+cudaError_t launch_potential_spectrum(const Plan& p, const double* placed, void* scratch, T* spec, cudaStream_t s) {
+    const int Px = p.ax.P, Py = p.ay.P;
+    Tiled t;
+    t.tw = RowCfg<double>::TW;
+    t.slab = (size_t)Px * t.tw;
+    cpx<double>* z = reinterpret_cast<cpx<double>*>(scratch);
+    cudaError_t e;
+    cpx<double>* tw64x = z + (size_t)((p.hy + t.tw - 1) / t.tw) * t.slab;
+    cpx<double>* tw64y = tw64x + Px;
+    if ((e = launch_twiddles<double>(tw64x, Px, s)) != cudaSuccess) return e;
+    if ((e = launch_twiddles<double>(tw64y, Py, s)) != cudaSuccess) return e;
+    const double scale = -p.G / ((double)Px * (double)Py);  // Phi = -G (C * w^phi)
+    size_t sm = col_smem<double>(Px);
+    if ((e = set_smem(k_cols_spectrum<T>, sm)) != cudaSuccess) return e;
+    int nt = round_threads(Px, kColThreads);
+    if ((e = rows_r2c<double>(placed, Px, Py, Py, 0, p.ay.half, tw64y, z, t, p.hy, s)) != cudaSuccess) return e;
+    k_cols_spectrum<T><<<p.hy, nt, sm, s>>>(z, t, p.hy, p.ax.full, tw64x, scale, 1, spec);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_potential(const Plan& p, const T* sigma, T* phi, void* work, cudaStream_t s) {
+    const Tiled t = tiled_of<T>(p, p.nx);
+    const size_t n_el = (size_t)p.ntile * t.slab;
+    cpx<T>* z = reinterpret_cast<cpx<T>*>(work);
+    cpx<T>* g = z + n_el;
+    const cpx<T>* twx = reinterpret_cast<const cpx<T>*>(p.tw_x);
+    const cpx<T>* twy = reinterpret_cast<const cpx<T>*>(p.tw_y);
+    const int solve = solve_order(p);
+    cudaError_t e = rows_r2c<T>(sigma, p.nx, p.ny, p.ny, solve, p.ay.half, twy, z, t, p.hy, s);
+    if (e != cudaSuccess) return e;
+    size_t sm = col_smem<T>(p.ax.full.L);
+    if ((e = set_smem(k_cols_pot<T>, sm)) != cudaSuccess) return e;
+    int nt = round_threads(p.ax.full.L, kColThreads);
+    k_cols_pot<T><<<p.hy, nt, sm, s>>>(z, t, p.nx, p.hy, solve, p.ax.full, twx,
+                                       reinterpret_cast<const T*>(p.spec_phi), g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return rows_c2r<T>(g, nullptr, t, p.nx, p.hy, 0, p.ay.half, twy, phi, nullptr, p.ny, s);
+}
+
+template cudaError_t launch_potential_spectrum<float>(const Plan&, const double*, void*, float*, cudaStream_t);
+template cudaError_t launch_potential_spectrum<double>(const Plan&, const double*, void*, double*, cudaStream_t);
+template cudaError_t launch_potential<float>(const Plan&, const float*, float*, void*, cudaStream_t);
+template cudaError_t launch_potential<double>(const Plan&, const double*, double*, void*, cudaStream_t);
 template cudaError_t launch_twiddles<float>(cpx<float>*, int, cudaStream_t);
 template cudaError_t launch_twiddles<double>(cpx<double>*, int, cudaStream_t);
 template cudaError_t launch_forward<float>(const Plan&, const float*, float*, float*, void*, cudaStream_t);

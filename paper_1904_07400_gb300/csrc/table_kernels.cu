@@ -75,6 +75,44 @@ cudaError_t launch_place_tables(const Plan& p, const double* wq, double* placed_
     return cudaGetLastError();
 }
 
+// the potential kernel's quadrant, placed even-even on the periodic grid
+__global__ void k_build_phi_table(int k, int nx, int ny, double dx, double dy, GLSet g, double* __restrict__ placed,
+                                  int Px, int Py) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nx * ny) return;
+    int m = (int)(idx / ny), n = (int)(idx % ny);
+    GLRule rules[kNumOrders];
+    int off = 0;
+    for (int i = 0; i < kNumOrders; ++i) {
+        rules[i].x = g.x + off;
+        rules[i].w = g.w + off;
+        rules[i].q = rule_order(i);
+        off += rule_order(i);
+    }
+    const double w = entry_phi(k, m, n, dx, dy, rules);
+    for (int sm = 0; sm < 2; ++sm) {
+        if (sm && m == 0) continue;
+        int im = sm ? Px - m : m;
+        for (int sn = 0; sn < 2; ++sn) {
+            if (sn && n == 0) continue;
+            int in = sn ? Py - n : n;
+            placed[(size_t)im * Py + in] = w;
+        }
+    }
+}
+
+cudaError_t launch_build_phi_table(const Plan& p, double* placed, const double* glx, const double* glw,
+                                   cudaStream_t s) {
+    GLSet g;
+    g.x = glx;
+    g.w = glw;
+    long n = (long)p.nx * p.ny;
+    int nt = 128;
+    k_build_phi_table<<<(unsigned)((n + nt - 1) / nt), nt, 0, s>>>(p.order, p.nx, p.ny, p.dx, p.dy, g, placed,
+                                                                   p.ax.P, p.ay.P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_tables(const Plan& p, double* wq, double* placed_x, double* placed_y, const double* glx,
                                 const double* glw, cudaStream_t s) {
     GLSet g;

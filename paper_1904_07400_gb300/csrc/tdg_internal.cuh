@@ -79,11 +79,20 @@ struct Plan {
     bool work_owned;
     int* err;              // device error word
     double* diag;          // diagnostics: block partials and the six norms (on first use)
+    void* spec_phi;        // potential spectrum (-G s_phi / (P_x P_y)), hy x P_x reals, on request
     int n_ev;              // 0 or 4: events recorded around the passes (instrumentation)
     cudaEvent_t ev[4];
 };
 
 // record the plan's instrumentation event i on stream s (no-op when none are set)
+// the potential (a diagnostic): table, spectrum, solve
+cudaError_t launch_build_phi_table(const Plan& p, double* placed, const double* glx, const double* glw,
+                                   cudaStream_t s);
+template <typename T>
+cudaError_t launch_potential_spectrum(const Plan& p, const double* placed, void* scratch, T* spec, cudaStream_t s);
+template <typename T>
+cudaError_t launch_potential(const Plan& p, const T* sigma, T* phi, void* work, cudaStream_t s);
+
 // radial-force diagnostics (diagnostics.cu): at most kDiagMaxBlocks partial sums
 constexpr int kDiagMaxBlocks = 1024;
 int diag_blocks(const Plan& p);

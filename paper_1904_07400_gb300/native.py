@@ -26,6 +26,8 @@ SIGNATURES = [
                           _c_double, _c_int, _c_int]),
     ("tdg_build_kernel_tables", _c_int, [_c_void_p, _c_void_p]),
     ("tdg_build_kernel_tables_from", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p]),
+    ("tdg_build_potential_tables", _c_int, [_c_void_p, _c_void_p]),
+    ("tdg_solve_potential", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_radial_diagnostics", _c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_double, ctypes.c_double,
                                         _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_workspace_bytes", _c_size_t, [_c_void_p]),

@@ -202,3 +202,24 @@ def test_radial_diagnostics_argument_checks(lib):
     assert f(h, a, a, 0.0, 0.0, None, a, None, None, None) == 1               # reference, no norms
     assert f(h, a, a, 0.0, 0.0, None, None, a, n, None) == 1                  # ref_fr without ref_fx
     lib.tdg_destroy(h)
+
+
+def test_potential_entry_host_matches_oracle(lib):
+    from oracle import kernel_tables as kt
+    for k in (1, 3, 5):
+        nf = kt.near_field_size(k)
+        for (m, n) in [(0, 0), (1, 0), (0, 2), (2, 1), (nf - 1, nf - 1)]:
+            got = native.kernel_entry_host(k, m, n, 1.0, 1.0, 2)
+            ref = kt._near_phi(k, m, n, 1.0)
+            assert abs(got - ref) < 5e-15 * ref, (k, m, n)
+        rng = np.random.default_rng(k)
+        for m, n in zip(rng.integers(0, 300, 20), rng.integers(0, 300, 20)):
+            if max(m, n) < nf:
+                continue
+            d = float(kt.band_distance(k, m, n, 1.0, 0.75))
+            q = [q for lim, q in kt.FAR_BANDS if lim is None or d < lim][0]
+            ref = kt.w_phi_far_gl(k, np.array([m]), np.array([n]), 1.0, 0.75, q)[0]
+            got = native.kernel_entry_host(k, int(m), int(n), 1.0, 0.75, 2)
+            assert abs(got - ref) < 5e-15 * ref
+        # even in m and n
+        assert native.kernel_entry_host(k, -3, 2, 1.0, 1.0, 2) == native.kernel_entry_host(k, 3, -2, 1.0, 1.0, 2)
