@@ -88,6 +88,62 @@ def max_over_ranks(x, world):
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (read-only queries) by a thread
+    polling every 2 ms while the timed region runs, so even a short region gets samples.
+    Reason bits are NVML's clocks-event-reason constants."""
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, index):
+        import ctypes
+        import threading
+        self.ct, self.threading = ctypes, threading
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib = lib
+        self.h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+        self.rows, self.stop_flag, self.thread = [], None, None
+
+    def _poll(self):
+        ct = self.ct
+        mhz, mask = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0 and \
+                    self.reasons_fn(self.h, ct.byref(mask)) == 0:
+                self.rows.append((float(mhz.value), int(mask.value)))
+            self.stop_flag.wait(0.002)
+
+    def start(self):
+        self.rows = []
+        self.stop_flag = self.threading.Event()
+        self.thread = self.threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        if not self.rows:
+            return None
+        reasons = sorted({n for _, m in self.rows for n, b in self.BITS.items() if m & b})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                "sm_max_mhz": self.max_mhz if self.max_mhz else max(r[0] for r in self.rows),
+                "samples": len(self.rows), "reasons": reasons, "source": "nvml"}
+
+
+def make_clocks(index):
+    try:
+        return NvmlClocks(index)
+    except Exception:
+        return Clocks(index)
+
+
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -131,7 +187,7 @@ class Clocks:
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "samples": len(rows), "reasons": reasons}
+                "samples": len(rows), "reasons": reasons, "source": "nvidia-smi"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -315,7 +371,7 @@ def run_ours(args):
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     results, outputs = {}, {}
     for i, form in enumerate(forms):
-        clocks = Clocks(local) if i == 0 else None
+        clocks = make_clocks(local) if i == 0 else None
         results[form], outputs[form] = time_form(form, sigma, n, args.steps, args.warmup, world, rank, clocks)
 
     head = forms[0]
