@@ -167,3 +167,17 @@ def test_network_path_orders_4_5(shape, k):
     a32 = to_np(p32.adjoint(t(gx, p32), t(gy, p32)))
     a64 = to_np(p64.adjoint(t(gx, p64), t(gy, p64)))
     assert np.linalg.norm(a32 - a64) / np.linalg.norm(a64) <= TOL_FP32
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_network_path_nonsquare_cells(k):
+    # cells with dy = 0.7 dx on the network path against the FP64 generic form
+    nx, ny = 384, 256
+    dx = 1.0 / nx
+    dy = 0.7 * dx
+    sigma = syn.clumps(nx, ny, seed=50 + k)
+    p32 = _plan(nx, ny, k, dx, dy, "fp32")
+    assert p32.path() == 2
+    f32 = _solve(p32, sigma)
+    f64 = _solve(_plan(nx, ny, k, dx, dy, "fp64"), sigma)
+    assert rel_l2_pair(*f32, *f64) <= TOL_FP32
