@@ -29,7 +29,9 @@ def _noalloc(plan, sigma, fx, fy):
 
 
 @pytest.mark.parametrize("shape,k,prec,tol", [((256, 192), 3, "fp32", TOL_FP32),
-                                             ((96, 160), 2, "fp64", TOL_FP64)])
+                                             ((96, 160), 2, "fp64", TOL_FP64),
+                                             ((256, 256), 5, "fp32", TOL_FP32),
+                                             ((100, 60), 4, "fp64", TOL_FP64)])
 def test_noalloc_matches_solve_on_two_calls_in_a_row(shape, k, prec, tol):
     import torch
     nx, ny = shape
