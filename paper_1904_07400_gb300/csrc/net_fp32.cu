@@ -494,10 +494,10 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // Shared memory: E = network buffer, later the row's cells for the TMA store; U = the
 // float row for the solve's transposition, later Z in padded natural order; edge.
 // ---------------------------------------------------------------------------------------
-// ORD: the order of the row solve (0: none)
+// ORD: the order of the row solve (0: none), or -1: the order `ord` given at run time
 template <int L, int ORD>
 __global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows(const float* __restrict__ sigma, int ny, int rowmap, int nx, const cf* __restrict__ nb,
+    k_net_rows(const float* __restrict__ sigma, int ny, int ord, int rowmap, int nx, const cf* __restrict__ nb,
                const cf* __restrict__ tw, const __grid_constant__ CUtensorMap zmap, cf* __restrict__ z) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
@@ -510,7 +510,8 @@ __global__ void __launch_bounds__(L / 16, 3)
     const net::Bases bs = net::load_bases<L>(nb, t);
     cf v[16];
     const int nact = ny >> 4;  // threads owning a 16-value chunk of the row
-    if constexpr (ORD != 0) {
+    const bool solve = ORD < 0 ? ord != 0 : ORD != 0;
+    if (solve) {
         // thread t owns s[16 t .. 16 t + 15]; past the row: zeros
         const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * ny) + 4 * t;
         float x[16];
@@ -522,7 +523,10 @@ __global__ void __launch_bounds__(L / 16, 3)
             x[4 * q + 2] = f.z;
             x[4 * q + 3] = f.w;
         }
-        solve_chunk_o<ORD, float>(x, t, nact, T, edge);
+        if constexpr (ORD < 0)
+            solve_chunk<float>(x, t, nact, T, edge, ord);
+        else if constexpr (ORD != 0)
+            solve_chunk_o<ORD, float>(x, t, nact, T, edge);
         // chunk -> natural-strided pairs through U (float index f at f + 4 (f / 32))
         float* uf = reinterpret_cast<float*>(U);
 #pragma unroll
@@ -783,10 +787,17 @@ constexpr size_t cols_smem_bytes() {
 }
 
 // column length nx <= L (a multiple of 16); Z, G_x, G_y hold nx rows
-// ORD: the order of the column solve (0: none)
+// ORD: the order of the column solve (0: none), or -1: the order `ord` given at run time.
+// 1024-cell columns keep five blocks an
+// SM (registers capped at 204), as they had before the solve order was compiled in: the
+// batched streams form relies on blocks of many small grids sharing the SMs
+template <int L>
+constexpr int cols_min_blocks() {
+    return L == 1024 ? 5 : 2;
+}
 template <int L, int ORD>
-__global__ void __launch_bounds__(L / 16, 2)
-    k_net_cols(const cf* __restrict__ z, int nx, const cf* __restrict__ nb, const cf* __restrict__ tw,
+__global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
+    k_net_cols(const cf* __restrict__ z, int nx, int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
                const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
@@ -819,11 +830,15 @@ __global__ void __launch_bounds__(L / 16, 2)
     const net::Bases bs = net::load_bases<L>(nb, t);
     const int nact = nx >> 4;
     cf v[16];
-    if constexpr (ORD != 0) {
+    const bool solve = ORD < 0 ? ord != 0 : ORD != 0;
+    if (solve) {
 #pragma unroll
         for (int r = 0; r < 16; ++r)  // row 16 t + r sits at r (nx / 16) + t
             v[r] = t < nact ? ld2(zc + (size_t)(r * nact + t) * kTW) : mk(0.f, 0.f);
-        solve_chunk_o<ORD, cf>(v, t, nact, T, edge);
+        if constexpr (ORD < 0)
+            solve_chunk<cf>(v, t, nact, T, edge, ord);
+        else if constexpr (ORD != 0)
+            solve_chunk_o<ORD, cf>(v, t, nact, T, edge);
 #pragma unroll
         for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = v[r];
         tmem_fence_before();
@@ -1284,14 +1299,20 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
 
     size_t sm = rows_bytes<LY>();
-    if ((e = set_smem(k_net_rows<LY, ORD>, sm))) return e;
+    // the order is compiled into the 4096-length kernels (pass B issues faster); shorter
+    // lengths share one instance for every order (the batched streams form runs many of
+    // them side by side, and one instance keeps their code footprint small)
+    constexpr int OR = LY == 4096 ? ORD : -1;
+    constexpr int OC = LX == 4096 ? ORD : -1;
+    const int ord = solve_order(p);
+    if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY, ORD><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ORD != 0, p.nx, bases_y(p), twy, zmap, z);
+    k_net_rows<LY, OR><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ord, ord != 0, p.nx, bases_y(p), twy, zmap, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_smem_bytes<LX>();
-    if ((e = set_smem(k_net_cols<LX, ORD>, sm))) return e;
-    k_net_cols<LX, ORD><<<hy, LX / 16, sm, s>>>(z, p.nx, bases_x(p), twx,
+    if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
+    k_net_cols<LX, OC><<<hy, LX / 16, sm, s>>>(z, p.nx, ord, bases_x(p), twx,
                                            reinterpret_cast<const float2*>(p.spec_half), gx, gy);
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
@@ -1339,9 +1360,9 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     size_t sm = rows_bytes<LY>();
     if ((e = set_smem(k_net_rows<LY, 0>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, p.nx, bases_y(p), twy, zmx, zx);
+    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmx, zx);
     if ((e = cudaGetLastError())) return e;
-    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, p.nx, bases_y(p), twy, zmy, zy);
+    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmy, zy);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_adj_smem_bytes<LX>();
