@@ -199,8 +199,8 @@ class Clocks:
 # (FP32 network path, 4096x4096, order 3).  Valid only for the kernel sources it was taken
 # on: reported when their SHA-256 still matches, null otherwise.
 MEASURED_TRAFFIC = {
-    ("cols_conv", 2, 4096): {"bytes": 268_841_472 + 216_026_112,
-                             "sha256": "8c3da722b899787d9a83273a46052ed778430985c2c00c8950ace50b65b6eee4"},
+    ("cols_conv", 2, 4096): {"bytes": 268_804_352 + 212_028_160,
+                             "sha256": "557f988e10fc84e63a93ab2b1bd535be329cda110e9e2394ff25db9482471f83"},
 }
 TRAFFIC_SOURCES = ("paper_1904_07400_gb300/csrc/net_fp32.cu", "paper_1904_07400_gb300/csrc/fft_net.cuh",
                    "paper_1904_07400_gb300/csrc/fft_reg.cuh")
