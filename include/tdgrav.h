@@ -5,7 +5,7 @@
  * What a solve computes (paper Eqs. eqnSigma, eqnF, eqnw, eqnwB):
  *   C          = B-spline coefficients of sigma at order k (Sec. 2.3: C = sigma for k = 1, 2;
  *                two truncated tridiagonal solves, Eqs. z_system and C_system, for k = 3;
- *                for k = 4, 5, the extension Sec. 2.3 and Sec. 4.2 call straightforward,
+ *                for k = 4, 5, the extension Sec. 2.2 and Sec. 2.3 call straightforward,
  *                the same interpolation condition with the stencils (1, 4, 1)/6 and
  *                (1, 76, 230, 76, 1)/384: truncated banded solves along y, then x)
  *   F^x_ij     = G * sum_{i'j'} C_{i'j'} w^x(i - i', j - j')

@@ -12,7 +12,7 @@ Paper references:
   * Eq. (C_system) - (1/64) tridiag(1,6,1) C = z along i, one system per j.
   * Isolated boundary condition C_ij = 0 outside the grid: the tridiagonal systems are the
     truncated ones (first and last rows keep only two entries).
-  * Orders 4 and 5 (the paper calls the extension straightforward, Sec. 2.3 and Sec. 4.2):
+  * Orders 4 and 5 (the paper calls the extension straightforward, Sec. 2.2 and Sec. 2.3):
     the same interpolation condition, sum_i' C_i' b_k(i - i') = s_i along each axis with
     C = 0 outside, whose stencil is b_k at the integer offsets: (1, 4, 1)/6 for k = 4
     (knots at cell centres) and (1, 76, 230, 76, 1)/384 for k = 5 (knots at faces).  One
