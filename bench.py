@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-depth", type=int, default=3,
                     help="end-to-end steps in flight (one stream and workspace each)")
+    ap.add_argument("--next2", action="store_true",
+                    help="time the in-simulation reuse pieces on the workload grid instead: a table "
+                         "build against a rebuild from kept tables, the potential solve and the "
+                         "radial diagnostics")
     ap.add_argument("--batched", action="store_true",
                     help="time the uneven batch (256 grids, one persistent launch) instead")
     return ap.parse_args()
@@ -579,6 +583,78 @@ def run_batched(args):
 E2E_DEPTH = 3
 
 
+def run_next2(args):
+    """One JSON line: the reuse pieces on the workload grid (FP32 plan, device-resident data).
+    Builds are timed with host clocks around the synchronising build calls; the potential
+    and the diagnostics with CUDA events over K calls after W warm-up calls."""
+    import numpy as np
+    import torch
+    from oracle.analytic import cartesian_force
+    from paper_1904_07400_gb300.api import Plan
+    from workloads import synthetic as syn
+
+    n, k = args.size, ORDER
+    d = 1.0 / n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    plan = Plan(n, n, k, d, d, precision="fp32", device=dev)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "tables.npz")
+        plan.save_tables(path)
+        t0 = time.perf_counter()
+        again = Plan(n, n, k, d, d, precision="fp32", device=dev, tables=path)
+        torch.cuda.synchronize()
+        t_from = time.perf_counter() - t0
+    again.close()
+    t0 = time.perf_counter()
+    plan.build_potential()
+    torch.cuda.synchronize()
+    t_pot_build = time.perf_counter() - t0
+    x, y, _, _ = syn.grid(n, n)
+    sigma = torch.as_tensor(syn.maclaurin_density(3, x, y, 0.4), dtype=torch.float32, device=dev)
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    ax, _, ar = cartesian_force(3, X, Y, 0.4)
+    ref_x = torch.as_tensor(ax, dtype=torch.float32, device=dev)
+    ref_r = torch.as_tensor(ar, dtype=torch.float32, device=dev)
+    fx, fy = plan.forces(sigma)
+    phi = torch.empty_like(sigma)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_pot = timed(lambda: plan.potential(sigma, out=phi))
+    ms_diag = timed(lambda: plan.radial_diagnostics(fx, fy, -0.5, -0.5))  # F_R only: asynchronous
+    # with the norms each call copies six values to the host and synchronises
+    ms_norms = timed(lambda: plan.radial_diagnostics(fx, fy, -0.5, -0.5, ref_x, ref_r, want_fr=True))
+    _, norms = plan.radial_diagnostics(fx, fy, -0.5, -0.5, ref_x, ref_r)
+    line = {"metric": "in-simulation reuse pieces, FP32 plan", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": f"{n}x{n} order-{k}, D3 disk (a = 0.4) for the diagnostics", "nx": n, "ny": n,
+                       "order": k},
+            "table_build_s": round(t_build, 4), "build_from_kept_tables_s": round(t_from, 4),
+            "potential_tables_build_s": round(t_pot_build, 4),
+            "potential_ms": round(ms_pot, 4), "potential_Mpts_s": round(n * n / (ms_pot * 1e-3) / 1e6, 1),
+            "radial_force_ms": round(ms_diag, 4),
+            "radial_force_GB_s": round(3 * 4 * n * n / (ms_diag * 1e-3) / 1e9, 1),
+            "radial_force_and_norms_ms": round(ms_norms, 4),
+            "radial_force_and_norms_GB_s": round(5 * 4 * n * n / (ms_norms * 1e-3) / 1e9, 1),
+            "norms_fx_fr_vs_analytic": [float(f"{v:.4e}") for v in norms],
+            "device_error": plan.device_error()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global E2E_DEPTH, ORDER, METRIC, WORKLOAD
     args = parse()
@@ -589,6 +665,9 @@ def main():
         ORDER = args.order
     if args.batched:
         run_batched(args)
+        return
+    if args.next2:
+        run_next2(args)
         return
     if args.impl == "reference":
         run_reference(args)

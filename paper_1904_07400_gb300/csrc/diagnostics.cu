@@ -2,10 +2,10 @@
 // measures F^x and F_R = (x F^x + y F^y) / R against the analytic forces of the
 // generalized Maclaurin disks, with one-, two- and infinity-norms, Sec. 3.1).
 //
-// One grid-stride pass over the cells writes F_R (if asked) and accumulates, per block in
-// FP64, sum |e|, sum e^2 and max |e| of e_x = F^x - ref_x and e_R = F_R - ref_R; a second
-// one-block pass reduces the block partials in a fixed order (the result does not depend
-// on timing).  The norms are area-weighted: L1 = dx dy sum |e|, L2 = (dx dy sum e^2)^(1/2),
+// One grid-stride pass over the cells writes F_R (if asked) and accumulates sum |e|,
+// sum e^2 and max |e| of e_x = F^x - ref_x and e_R = F_R - ref_R, per thread in the data's
+// precision (compensated for FP32), per block in FP64; a second one-block pass reduces the
+// block partials in a fixed order (the result does not depend on timing).  The norms are area-weighted: L1 = dx dy sum |e|, L2 = (dx dy sum e^2)^(1/2),
 // Linf = max |e|.
 #include <cuda_runtime.h>
 
@@ -19,16 +19,6 @@ constexpr int kDiagThreads = 256;
 struct Acc6 {
     double v[6];  // sum|ex|, sum ex^2, max|ex|, sum|er|, sum er^2, max|er|
 };
-
-__device__ __forceinline__ void acc_add(Acc6& a, double ex, double er) {
-    const double ax = fabs(ex), ar = fabs(er);
-    a.v[0] += ax;
-    a.v[1] += ex * ex;
-    a.v[2] = fmax(a.v[2], ax);
-    a.v[3] += ar;
-    a.v[4] += er * er;
-    a.v[5] = fmax(a.v[5], ar);
-}
 
 // block-wide reduction of six values into red[0..5] (thread 0 holds the result)
 __device__ void block_reduce(Acc6 a, double* red) {
@@ -47,24 +37,75 @@ __device__ void block_reduce(Acc6 a, double* red) {
         for (int q = 0; q < 6; ++q) red[q] = sh[q][0];
 }
 
+// per-thread sums: FP64 for FP64 data; for FP32 data, FP32 with compensated (Kahan)
+// additions, so that the per-cell work stays on the FP32 pipes (FP64 arithmetic is slow on
+// this part) while each thread's sums keep about FP32 precision; blocks reduce in FP64
+template <typename T>
+struct ThreadSums {
+    T s[4], comp[4], mx[2];  // sum|ex|, sum ex^2, sum|er|, sum er^2; compensations; maxima
+    __device__ __forceinline__ ThreadSums() {
+        for (int q = 0; q < 4; ++q) s[q] = comp[q] = T(0);
+        mx[0] = mx[1] = T(0);
+    }
+    __device__ __forceinline__ void add(int q, T v) {
+        if constexpr (sizeof(T) == 8) {
+            s[q] += v;
+        } else {
+            const T y = v - comp[q];
+            const T t = s[q] + y;
+            comp[q] = (t - s[q]) - y;
+            s[q] = t;
+        }
+    }
+    __device__ __forceinline__ void push(T ex, T er) {
+        const T ax = fabs(ex), ar = fabs(er);
+        add(0, ax);
+        add(1, ex * ex);
+        add(2, ar);
+        add(3, er * er);
+        mx[0] = fmax(mx[0], ax);
+        mx[1] = fmax(mx[1], ar);
+    }
+    __device__ __forceinline__ Acc6 to_acc() const {
+        Acc6 a;
+        a.v[0] = (double)s[0] - (double)comp[0];
+        a.v[1] = (double)s[1] - (double)comp[1];
+        a.v[2] = (double)mx[0];
+        a.v[3] = (double)s[2] - (double)comp[2];
+        a.v[4] = (double)s[3] - (double)comp[3];
+        a.v[5] = (double)mx[1];
+        return a;
+    }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kDiagThreads) k_radial(int nx, int ny, double dx, double dy, double x0, double y0,
                                                          const T* __restrict__ fx, const T* __restrict__ fy,
                                                          T* __restrict__ fr, const T* __restrict__ rx,
                                                          const T* __restrict__ rr, double* __restrict__ part) {
-    Acc6 a;
-    for (int q = 0; q < 6; ++q) a.v[q] = 0.0;
+    ThreadSums<T> acc;
     const long n = (long)nx * ny;
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(c / ny), j = (int)(c % ny);
-        const double x = x0 + (i + 0.5) * dx, y = y0 + (j + 0.5) * dy;
-        const double R = sqrt(x * x + y * y);
-        const double gx = (double)fx[c];
-        const double g = R > 0.0 ? (x * gx + y * (double)fy[c]) / R : 0.0;
-        if (fr) fr[c] = (T)g;
-        if (rx) acc_add(a, gx - (double)rx[c], rr ? g - (double)rr[c] : 0.0);
+    const T tx0 = (T)x0, ty0 = (T)y0, tdx = (T)dx, tdy = (T)dy;
+    // (i, j) of cell c, advanced by the grid stride without a division per cell
+    const long stride = (long)gridDim.x * blockDim.x;
+    const int di = (int)(stride / ny), dj = (int)(stride % ny);
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = (int)(c / ny), j = (int)(c % ny);
+    for (; c < n; c += stride) {
+        const T x = tx0 + (T)(i + 0.5) * tdx, y = ty0 + (T)(j + 0.5) * tdy;
+        const T R = sqrt(x * x + y * y);
+        const T gx = fx[c];
+        const T g = R > T(0) ? (x * gx + y * fy[c]) / R : T(0);
+        if (fr) fr[c] = g;
+        if (rx) acc.push(gx - rx[c], rr ? g - rr[c] : T(0));
+        i += di;
+        j += dj;
+        if (j >= ny) {
+            j -= ny;
+            ++i;
+        }
     }
-    if (part) block_reduce(a, part + 6 * blockIdx.x);
+    if (part) block_reduce(acc.to_acc(), part + 6 * blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kDiagThreads) k_reduce6(int nblocks, double area, const double* __restrict__ part,
