@@ -418,12 +418,15 @@ def _inner_phi(k: int, m: int, h: float, v):
     return total
 
 
-def w_phi_route(k: int, m: int, n: int, dx: float, dy: float, dps: int = 30):
+def w_phi_route(k: int, m, n: int, dx: float, dy: float, dps: int = 30, k_v: int | None = None):
     """w^phi at one offset: the u-integral in closed form, then an mpmath quadrature in v
-    split at v = 0 (a logarithmic endpoint singularity) and at the knots."""
+    split at v = 0 (a logarithmic endpoint singularity) and at the knots.  With k_v the
+    spline along v has that order instead (the mixed integrals of the force-potential
+    identity, where m may also be a half-integer)."""
+    kv = k if k_v is None else k_v
     with mp.workdps(dps):
         total = mp.mpf(0)
-        for lo, hi, cs in pieces_exact(k):
+        for lo, hi, cs in pieces_exact(kv):
             vl, vh = (_mpf(lo) - n) * mp.mpf(dy), (_mpf(hi) - n) * mp.mpf(dy)
             pts = [vl, vh]
             if vl < 0 < vh:

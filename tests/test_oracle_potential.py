@@ -95,3 +95,18 @@ def test_potential_order_of_accuracy():
             l2.append(paper_norms(phi - ref, dx, dy)[1])
         o = orders(l2)[-1]
         assert abs(o - o_exp) < 0.15, (k, l2, o)
+
+
+@pytest.mark.parametrize("k,m,n", [(2, 3, 2), (3, 4, 2), (4, 3, 3), (5, 4, 3)])
+def test_force_kernel_is_the_potential_difference(k, m, n):
+    # u r^-3 = -d/du (1/r) and b_k' = b_{k-1}(t + 1/2) - b_{k-1}(t - 1/2), so
+    # w^x_k(m, n) = (1/dx) [Phi_{k-1,k}(m + 1/2, n) - Phi_{k-1,k}(m - 1/2, n)] with Phi the
+    # potential integral of orders (k-1, k): the potential route against the paper's closed
+    # forms (route P) for the force kernel
+    import mpmath as mp
+    dx = 1.0
+    with mp.workdps(25):
+        rhs = (kt.w_phi_route(k - 1, m + 0.5, n, dx, 1.0, dps=25, k_v=k)
+               - kt.w_phi_route(k - 1, m - 0.5, n, dx, 1.0, dps=25, k_v=k)) / dx
+    lhs = kt.w_route_p(k, m, n, dx, 1.0, "x")
+    assert abs(lhs - rhs) < mp.mpf(10) ** -15 * abs(lhs)
