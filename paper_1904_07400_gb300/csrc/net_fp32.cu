@@ -2,8 +2,8 @@
 // 4096 cells, padded to transform lengths L in {512, 1024, 2048, 4096}, built around the
 // one-barrier register FFT network of fft_net.cuh and the data movement of sm_103a:
 //
-//  * pass A (rows): chunked register spline solve, packed real transform, unpack, and a
-//    TMA bulk-tensor store of the row into the tiled intermediate Z;
+//  * pass A (rows): chunked register spline solve, packed real transform, unpack, and
+//    16-byte stores of the row's cells into the tiled intermediate Z;
 //  * pass B (columns): chunked register spline solve, the zero-padded column transform as
 //    two half-length transforms (even and odd frequencies), both spectrum products and
 //    four inverse half-length transforms, with the spectra stored in the network's
@@ -350,18 +350,6 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// the shared-memory sources of every committed bulk store have been read (the global
-// writes finish on their own before the grid completes)
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 __device__ __forceinline__ void flag_error(int* err, int code) {
     if (err) atomicCAS(err, 0, code);
 }
@@ -491,14 +479,18 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // ---------------------------------------------------------------------------------------
 // pass A: one row i per block (T = L / 16 threads); row length L = ny, transformed as the
 // packed complex sequence z_n = s_2n + i s_2n+1 of length L (period 2L, upper half zero).
-// Shared memory: E = network buffer, later the row's cells for the TMA store; U = the
-// float row for the solve's transposition, later Z in padded natural order; edge.
+// Shared memory: E = network buffer; U = the float row for the solve's transposition, later
+// Z in padded natural order for the unpack; edge.  Each thread unpacks its cells
+// (X[2p], X[2p+1]), p = t + T q, and stores them from registers with 16-byte stores: per
+// row there are L/2 cells, one per two-column tile, so every store touches its own tile
+// whichever unit issues it, and storing from registers needs neither a staging buffer nor
+// the block to wait for a bulk copy before it exits.
 // ---------------------------------------------------------------------------------------
 // ORD: the order of the row solve (0: none), or -1: the order `ord` given at run time
 template <int L, int ORD>
 __global__ void __launch_bounds__(L / 16, 3)
     k_net_rows(const float* __restrict__ sigma, int ny, int ord, int rowmap, int nx, const cf* __restrict__ nb,
-               const cf* __restrict__ tw, const __grid_constant__ CUtensorMap zmap, cf* __restrict__ z) {
+               const cf* __restrict__ tw, cf* __restrict__ z) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -551,13 +543,17 @@ __global__ void __launch_bounds__(L / 16, 3)
 #pragma unroll
     for (int c = 8; c < 16; ++c) v[c] = mk(0.f, 0.f);
     net::fwd<L>(v, E, bs, t);
-    // Z (network order) -> U, natural padded
+    // Z (network order) -> U, natural padded (every thread read its pairs from U before the
+    // barrier inside fwd)
     const int pt = net::perm<L>(t);
 #pragma unroll
     for (int ka = 0; ka < 16; ++ka) U[pad(pt + T * ka)] = v[ka];
     const float znyq = v[0].x - v[0].y;  // X[L] (thread 0: v[0] = Z[0])
     __syncthreads();
-    // cells p = t + T q: (X[2p], X[2p+1]) with X[k] = unpack(Z[k], Z[L-k], W_2L^k)
+    // cells p = t + T q: (X[2p], X[2p+1]) with X[k] = unpack(Z[k], Z[L-k], W_2L^k), stored to
+    // tile p of row position rp
+    const int rp = rowmap ? (i & 15) * (nx >> 4) + (i >> 4) : i;
+    cf* zr = z + (size_t)rp * kTW;
     const cf w2t = reg::ld_tw(tw, 2 * t);  // W_2L^(2t)
     const cf w1 = reg::ld_tw(tw, 1);       // W_2L
 #pragma unroll
@@ -568,18 +564,9 @@ __global__ void __launch_bounds__(L / 16, 3)
         const cf wk1 = cmul(wk0, w1);
         const cf x0 = unpack_r2c(U[pad(k0)], U[pad((L - k0) & (L - 1))], wk0);
         const cf x1 = unpack_r2c(U[pad(k0 + 1)], U[pad(L - k0 - 1)], wk1);
-        *reinterpret_cast<float4*>(E + k0) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        *reinterpret_cast<float4*>(zr + (size_t)p * nx * kTW) = make_float4(x0.x, x0.y, x1.x, x1.y);
     }
-    fence_async_smem();
-    __syncthreads();
-    if (t == 0) {
-        const int rp = rowmap ? (i & 15) * (nx >> 4) + (i >> 4) : i;
-#pragma unroll 1
-        for (int b = 0; b < L / 2 / kBox; ++b) tma_store_3d(&zmap, 0, rp, b * kBox, E + 2 * b * kBox);
-        bulk_commit();
-        z[(size_t)(L / 2) * nx * kTW + (size_t)rp * kTW] = mk(znyq, 0.f);
-        bulk_wait_read();
-    }
+    if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1291,8 +1278,7 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
     cudaError_t e;
-    CUtensorMap zmap, gmap;
-    if ((e = encode_tiles(&zmap, z, p.nx, ntile, 1, 0))) return e;
+    CUtensorMap gmap;
     if ((e = encode_tiles(&gmap, gx, p.nx, ntile, 2, n_el * sizeof(cf)))) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev))) return e;
@@ -1307,7 +1293,7 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     const int ord = solve_order(p);
     if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY, OR><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ord, ord != 0, p.nx, bases_y(p), twy, zmap, z);
+    k_net_rows<LY, OR><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ord, ord != 0, p.nx, bases_y(p), twy, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_smem_bytes<LX>();
@@ -1350,9 +1336,7 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
     const int solve = solve_order(p);
     cudaError_t e;
-    CUtensorMap zmx, zmy, gmap;
-    if ((e = encode_tiles(&zmx, zx, p.nx, ntile, 1, 0))) return e;
-    if ((e = encode_tiles(&zmy, zy, p.nx, ntile, 1, 0))) return e;
+    CUtensorMap gmap;
     if ((e = encode_tiles(&gmap, g, p.nx, ntile, 1, 0, true))) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev))) return e;
@@ -1360,9 +1344,9 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     size_t sm = rows_bytes<LY>();
     if ((e = set_smem(k_net_rows<LY, 0>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmx, zx);
+    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, 0, p.nx, bases_y(p), twy, zx);
     if ((e = cudaGetLastError())) return e;
-    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, 0, p.nx, bases_y(p), twy, zmy, zy);
+    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, 0, p.nx, bases_y(p), twy, zy);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
     sm = cols_adj_smem_bytes<LX>();
