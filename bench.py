@@ -9,6 +9,8 @@ the library's C ABI.  Kernel tables are built once per plan before timing and ex
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+`--gpus N` (N > 1) from a plain `python bench.py` re-launches the script as N ranks with
+torch.distributed.run; under a launcher the world size must equal N.
 Headline `value`: FP32 form, Mpts/s (nx * ny output points per solve), inputs resident in
 HBM.  `e2e`: the same through the public API with the input copied from pinned host memory
 and both force components copied back every step.  `forms`: every precision form timed the
@@ -57,25 +59,69 @@ def parse():
                          "radial diagnostics")
     ap.add_argument("--batched", action="store_true",
                     help="time the uneven batch (256 grids, one persistent launch) instead")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="check the rank launch only: every rank joins a gloo group on the CPU and rank 0 "
+                         "prints the world size it saw (no GPU work)")
     return ap.parse_args()
+
+
+def launch_ranks(args):
+    """`--gpus N` with N > 1 from a plain `python bench.py` re-launches this script as N
+    ranks through torch.distributed.run (one process per GPU, 127.0.0.1 rendezvous); under a
+    launcher the world size must equal N."""
+    world = os.environ.get("WORLD_SIZE")
+    if world is not None:
+        if int(world) != args.gpus:
+            sys.exit(f"bench.py: --gpus {args.gpus} but the launcher started WORLD_SIZE={world} ranks")
+        return
+    if args.gpus <= 1:
+        return
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    env = dict(os.environ)
+    # NCCL's init log (to stderr, keeping stdout for the JSON line) shows the communicator size
+    env.setdefault("NCCL_DEBUG", "INFO")
+    env.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
+    env.setdefault("NCCL_DEBUG_FILE", "/dev/stderr")
+    sys.exit(subprocess.call(cmd, env=env))
 
 
 # ------------------------------------------------------------------------------------------
 # distributed plumbing (one process per GPU, replicas)
 # ------------------------------------------------------------------------------------------
 
-def dist_setup(n):
+def dist_setup(n, cpu=False):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+        if cpu:
+            dist.init_process_group("gloo")
+        else:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif not cpu:
         torch.cuda.set_device(0)
     return rank, world, local
+
+
+def run_dry(args):
+    """The multi-rank plumbing without GPU work: ranks, barrier and max over ranks."""
+    rank, world, _ = dist_setup(args.gpus, cpu=True)
+    barrier(world)
+    t = max_over_ranks(float(rank), world)
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "gpus_requested": args.gpus,
+                          "max_over_ranks_of_rank": t}), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def barrier(world):
@@ -199,9 +245,9 @@ class Clocks:
 # ------------------------------------------------------------------------------------------
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# dominant kernel, from the ncu capture summarised in profiles/net_kernels_fp32_4096_full.md
-# (FP32 network path, 4096x4096, order 3).  Valid only for the kernel sources it was taken
-# on: reported when their SHA-256 still matches, null otherwise.
+# dominant kernel, from one ncu capture of this workload (FP32 network path, 4096x4096,
+# order 3).  Valid only for the kernel sources it was taken on: reported when their SHA-256
+# still matches, null otherwise.
 MEASURED_TRAFFIC = {
     ("cols_conv", 2, 4096): {"bytes": 268_804_352 + 212_028_160,
                              "sha256": "557f988e10fc84e63a93ab2b1bd535be329cda110e9e2394ff25db9482471f83"},
@@ -353,14 +399,25 @@ def peaks():
         return None
 
 
-def oracle_solve(sigma, n):
-    """FP64 CPU oracle on the same grid; returns (forces, seconds for the solve alone)."""
+def oracle_solve(sigma, n, reps=3):
+    """FP64 CPU oracle on the same grid, timed on all host cores (scipy's pocketfft with
+    workers = os.cpu_count()) and on one thread (numpy's), best of `reps` each; returns
+    (forces, seconds all cores, seconds one thread, cores)."""
     from oracle.convolution import Solver
     S = Solver(n, n, ORDER, 1.0 / n, 1.0 / n)
     _ = S.spec  # tables and their transforms: built once, not timed
-    t = time.perf_counter()
-    f = S.forces(sigma)
-    return f, time.perf_counter() - t
+    cores = os.cpu_count() or 1
+
+    def best(workers):
+        out, secs = None, []
+        for _ in range(reps):
+            t = time.perf_counter()
+            out = S.forces(sigma, workers=workers)
+            secs.append(time.perf_counter() - t)
+        return out, min(secs)
+    f, t_all = best(cores)
+    _, t_one = best(None)
+    return f, t_all, t_one, cores
 
 
 def run_ours(args):
@@ -415,11 +472,14 @@ def run_ours(args):
                          "e2e_Mpts_s": round(world * pts / (results[f]["e2e_ms"] * 1e-3) / 1e6, 1)}
                      for f in forms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ref, secs = oracle_solve(sigma, n)
-        line["cpu_baseline"] = {"value": round(pts / secs / 1e6, 3), "unit": "Mpts/s", "cores": 1,
+        ref, t_all, t_one, cores = oracle_solve(sigma, n)
+        line["cpu_baseline"] = {"value": round(pts / t_all / 1e6, 3), "unit": "Mpts/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": f"one FP64 oracle solve of the same {n}x{n} grid (numpy pocketfft, "
-                                          "single thread), kernel tables built beforehand and not timed"}
+                                "single_thread_value": round(pts / t_one / 1e6, 3),
+                                "sample": f"FP64 oracle solves of the same {n}x{n} grid, best of 3: value on all "
+                                          f"{cores} host cores (scipy pocketfft, workers={cores}), "
+                                          "single_thread_value with numpy pocketfft on one thread; kernel tables "
+                                          "built beforehand and not timed"}
         for f in forms:
             line["forms"][f]["rel_l2_vs_oracle"] = float(f"{rel_l2(*outputs[f], *ref):.3e}")
     if "fp64" in outputs:
@@ -448,16 +508,19 @@ def run_reference(args):
     from oracle.convolution import Solver
     from workloads import synthetic as syn
 
-    # each step is one oracle solve of the same recipe; the grid is scaled down (by 2 per
-    # side at a time, from 4096) until the whole run is expected to take a few minutes
+    # each step is one oracle solve of the same recipe on all host cores (scipy's pocketfft
+    # with workers = os.cpu_count()); the grid is scaled down (by 2 per side at a time, from
+    # 4096) only if the whole run would not finish within a few minutes
+    cores = os.cpu_count() or 1
     budget = 150.0
     steps = args.steps + args.warmup
     n = min(args.size, 512)
     probe = Solver(n, n, ORDER, 1.0 / n, 1.0 / n)
     _ = probe.spec
     sig = syn.clumps(n, n, seed=SEED)
+    probe.forces(sig, workers=cores)
     t = time.perf_counter()
-    probe.forces(sig)
+    probe.forces(sig, workers=cores)
     per = time.perf_counter() - t
     while n * 2 <= args.size and per * 4.4 * steps < budget:
         n *= 2
@@ -466,13 +529,13 @@ def run_reference(args):
     _ = S.spec
     sigma = syn.clumps(n, n, seed=SEED)
     for _ in range(args.warmup):
-        S.forces(sigma)
+        S.forces(sigma, workers=cores)
     t = time.perf_counter()
     for _ in range(args.steps):
-        S.forces(sigma)
+        S.forces(sigma, workers=cores)
     secs = (time.perf_counter() - t) / args.steps
     value = n * n / secs / 1e6
-    sample = (f"each step one FP64 oracle solve (numpy pocketfft, single thread) of the {n}x{n} grid "
+    sample = (f"each step one FP64 oracle solve (scipy pocketfft on {cores} host threads) of the {n}x{n} grid "
               f"of the same recipe{'' if n == args.size else ' (scaled down from 4096x4096 to bound the run)'}")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3, 2),
@@ -480,7 +543,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD if n == N_GRID else WORKLOAD.replace("4096x4096", f"{n}x{n}"),
                        "nx": n, "ny": n, "order": ORDER, "form": "oracle-fp64-cpu"},
-            "cpu_baseline": {"value": round(value, 3), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 3), "unit": "Mpts/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -658,6 +721,10 @@ def run_next2(args):
 def main():
     global E2E_DEPTH, ORDER, METRIC, WORKLOAD
     args = parse()
+    launch_ranks(args)
+    if args.dry_run:
+        run_dry(args)
+        return
     E2E_DEPTH = args.e2e_depth
     if args.order != ORDER:
         METRIC = METRIC.replace("order-3", f"order-{args.order}")

@@ -10,7 +10,9 @@ Two evaluations of the same exact discrete result:
     one forward transform of C and two inverse transforms), with C and the tables placed
     on a zero-padded 2Nx x 2Ny periodic grid.  Circular convolution of period
     P >= 2N - 1 equals the linear one on the cropped window; offset +-N (index N) is never
-    reached and is set to zero.  numpy's pocketfft in FP64 is the library primitive.
+    reached and is set to zero.  pocketfft in FP64 is the library primitive: numpy's
+    (one thread), or scipy's when a thread count is given (the same transforms over the
+    rows and columns of the padded arrays, spread over host threads).
 
 Array convention: shape (Nx, Ny), axis 0 is x.  Tables are the full arrays of
 ``kernel_tables`` (shape (2Nx-1, 2Ny-1), index [m + Nx - 1, n + Ny - 1]).
@@ -55,15 +57,25 @@ def spectra(wx: np.ndarray, wy: np.ndarray, px: int, py: int):
             np.fft.rfft2(place_periodic(wy, px, py)))
 
 
-def forces_fft(c: np.ndarray, wx: np.ndarray, wy: np.ndarray, G: float = 1.0, spec=None):
+def _fft2(workers):
+    """(rfft2, irfft2) of the library: numpy's for workers None, else scipy's on that many
+    host threads."""
+    if workers is None:
+        return np.fft.rfft2, np.fft.irfft2
+    import scipy.fft as sf
+    return (lambda a, s: sf.rfft2(a, s=s, workers=workers)), (lambda a, s: sf.irfft2(a, s=s, workers=workers))
+
+
+def forces_fft(c: np.ndarray, wx: np.ndarray, wy: np.ndarray, G: float = 1.0, spec=None, workers=None):
     """Same result as ``forces_direct`` via zero-padded FFTs (1 forward + 2 inverse)."""
     nx, ny = c.shape
     px, py = 2 * nx, 2 * ny
     if spec is None:
         spec = spectra(wx, wy, px, py)
-    chat = np.fft.rfft2(c, s=(px, py))
-    fx = np.fft.irfft2(chat * spec[0], s=(px, py))[:nx, :ny]
-    fy = np.fft.irfft2(chat * spec[1], s=(px, py))[:nx, :ny]
+    rfft2, irfft2 = _fft2(workers)
+    chat = rfft2(c, s=(px, py))
+    fx = irfft2(chat * spec[0], s=(px, py))[:nx, :ny]
+    fy = irfft2(chat * spec[1], s=(px, py))[:nx, :ny]
     return G * fx, G * fy
 
 
@@ -134,11 +146,12 @@ class Solver:
     def coefficients(self, sigma):
         return bspline_coefficients(sigma, self.k)
 
-    def forces(self, sigma, method: str = "fft"):
+    def forces(self, sigma, method: str = "fft", workers=None):
+        """workers: host threads of the FFTs (None: numpy's single-threaded pocketfft)."""
         c = self.coefficients(sigma)
         if method == "direct":
             return forces_direct(c, self.wx, self.wy, self.G)
-        return forces_fft(c, self.wx, self.wy, self.G, self.spec)
+        return forces_fft(c, self.wx, self.wy, self.G, self.spec, workers)
 
     def forces_at(self, sigma, points):
         """F^x, F^y at a few output cells, each one by its own literal sum (any size)."""

@@ -129,3 +129,18 @@ def test_planted_transposed_tables_break_invariant():
     sig = sig + sig[::-1, :]
     fx, _ = forces_fft(sig, S.wy, S.wx)
     assert np.abs(fx + fx[::-1, :]).max() > 1e-3 * np.abs(fx).max()
+
+
+def test_threaded_fft_equals_direct_sum():
+    """The multi-threaded FFT primitive (scipy's pocketfft over host threads, used to time
+    the oracle on all cores) gives the direct double sum of Eq. (eqnF), like numpy's."""
+    import os
+    nx, ny, k = 20, 14, 3
+    rng = np.random.default_rng(11)
+    sigma = rng.standard_normal((nx, ny))
+    S = Solver(nx, ny, k, 1.0 / nx, 1.0 / nx)
+    rx, ry = S.forces(sigma, method="direct")
+    fx, fy = S.forces(sigma, workers=os.cpu_count() or 1)
+    scale = max(np.abs(rx).max(), np.abs(ry).max())
+    assert np.abs(fx - rx).max() < 1e-13 * scale
+    assert np.abs(fy - ry).max() < 1e-13 * scale
