@@ -11,12 +11,14 @@ the library's C ABI.  Kernel tables are built once per plan before timing and ex
 
 `--gpus N` (N > 1) from a plain `python bench.py` re-launches the script as N ranks with
 torch.distributed.run; under a launcher the world size must equal N.
+
 Headline `value`: FP32 form, Mpts/s (nx * ny output points per solve), inputs resident in
 HBM.  `e2e`: the same through the public API with the input copied from pinned host memory
 and both force components copied back every step.  `forms`: every precision form timed the
-same way, each with its relative L2 error against the FP64 CPU oracle (one oracle solve of
-the same grid, also reported as `cpu_baseline`).  With N > 1 (torchrun) each rank solves
-its own grid (independent replicas, no collective on the data path): weak scaling.
+same way, each with its relative L2 error against the FP64 CPU oracle (oracle solves of the
+same grid, timed on all host cores and on one thread, best of 3: `cpu_baseline`).  With
+N > 1 each rank solves its own grid (independent replicas, no collective on the data
+path): weak scaling.
 """
 from __future__ import annotations
 
