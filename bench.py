@@ -462,7 +462,7 @@ def run_ours(args):
                         "algorithmic_bytes": algo,
                         "pass_ms": {k: round(v, 4) for k, v in r["per_pass_ms"].items()},
                         "step_bytes": sum(pass_bytes(n, n, r["px"], r["real"], r["path"]).values()),
-                        "kernel_path": {0: "generic", 1: "register", 2: "network"}.get(r["path"], "generic")}
+                        "kernel_path": {0: "generic", 2: "network", 3: "network, tensor-core column pass"}.get(r["path"], "generic")}
     line["e2e"] = {"value": round(world * pts / (r["e2e_ms"] * 1e-3) / 1e6, 1), "unit": "Mpts/s",
                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
     line["gpu_launches"] = 3 * args.steps  # rows, columns, inverse rows per solve

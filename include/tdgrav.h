@@ -53,8 +53,9 @@ typedef enum {
 typedef enum {
     TDG_FP64 = 0,       /* every step in double                                          */
     TDG_FP32 = 1,       /* float transforms, spectra rounded from the FP64 build         */
-    TDG_FP32_TC16 = 2   /* float, radix-16 DFT stages as split FP16 hi/lo tensor-core
-                           products accumulated in FP32                                  */
+    TDG_FP32_TC16 = 2   /* float; the column pass runs its radix-16 DFT stages as split
+                           hi/lo tensor-core products (TF32 operands, tcgen05.mma),
+                           accumulated in FP32                                           */
 } tdg_precision;
 
 typedef struct tdg_plan_s* tdg_plan;
@@ -64,8 +65,9 @@ typedef struct CUstream_st* tdg_stream;
 /* Create a plan for an nx x ny grid of cells dx x dy, B-spline order 1..5, constant G.
  * Allocates nothing on the device yet.  Errors: INVALID_ARG for order not in 1..5,
  * nx or ny < 1, dx or dy not finite and > 0, G not finite, out == NULL; UNSUPPORTED for
- * nx or ny > 4096, and for TDG_FP32_TC16 with order > 3 or sides other than 1024, 2048,
- * 4096; CUDA if `device` cannot be selected. */
+ * nx or ny > 4096, and for TDG_FP32_TC16 unless both sides are multiples of 16 from 128
+ * to 4096 and nx > 1024 (the tensor-core column pass takes columns padded to 2048 or 4096
+ * cells); CUDA if `device` cannot be selected. */
 tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double dy,
                     double G, tdg_precision prec, int device);
 
@@ -239,16 +241,59 @@ tdg_status tdg_set_pass_events(tdg_plan p, void* const* events, int count);
 tdg_status tdg_solve_forces_noalloc(tdg_plan p, const void* sigma, void* fx, void* fy,
                                     tdg_stream stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Slab decomposition of one grid over `world` ranks (Sec. 2.3: the spline solves and the
+ * transforms are split over processes in slabs, with transposes between the passes).  For
+ * FP32 plans on the transform-network path (tdg_plan_path 2) with nx / 16 >= world.  Every
+ * rank builds the same plan on its own device; rank r owns rows [r0, r0 + nrows) of sigma
+ * and of the forces, and the two-column tiles [t0, t0 + ntiles) of frequency columns
+ * ky = 2 t0 .. (the last rank ends at the Nyquist column).  One solve, on every rank:
+ *   1. tdg_slab_rows_forward: sigma rows -> Z row slab;
+ *   2. all-to-all of the Z row slab: the chunk for rank q (tdg_slab_partition of q) is
+ *      ntiles_q * nrows_r cells at cell offset t0_q * nrows_r; chunks arrive in source order;
+ *   3. tdg_slab_unpack_z: the received chunks -> Z column slab;
+ *   4. tdg_slab_columns: Z column slab -> G column slab (G_x, then G_y);
+ *   5. tdg_slab_pack_g: G column slab -> send buffer, per component one chunk per destination
+ *      r of ntiles_self * nrows_r cells, in rank order;
+ *   6. all-to-all per component: the chunks received in source order are the G row slab
+ *      (component c at cell offset c * tdg_slab_bytes(..., 3) / 32);
+ *   7. tdg_slab_rows_inverse: G row slab -> force rows.
+ * A cell is 16 bytes (two complex floats).  Buffers are DEVICE pointers on the plan's device,
+ * owned by the caller, 16-byte aligned, sized by tdg_slab_bytes; all calls are asynchronous
+ * on `stream`.  The result equals tdg_solve_forces on the whole grid.  The paper has no
+ * library interface; these calls follow its distribution. */
+
+/* Rows and tiles of `rank` for an nx x ny grid (host only, no device).  Rows come in
+ * multiples of 16, the extra ones to the first ranks; tiles likewise.  Any out pointer may
+ * be NULL.  Errors: INVALID_ARG (sizes off the network path, world < 1, rank outside
+ * 0..world-1, fewer 16-row chunks or tiles than ranks). */
+tdg_status tdg_slab_partition(int nx, int ny, int world, int rank, int* r0, int* nrows, int* t0, int* ntiles);
+
+/* Bytes of one of rank's slab buffers: which = 0 Z row slab, 1 Z column slab (the received
+ * chunks of step 2 have the same size), 2 G column slab (= the send buffer of step 5),
+ * 3 G row slab (both components).  0 for a bad plan, rank or `which`. */
+size_t tdg_slab_bytes(const tdg_plan p, int world, int rank, int which);
+
+/* Steps 1, 3, 4, 5 and 7 above.  sigma_rows, fx_rows, fy_rows: nrows x ny floats, row-major
+ * (row r0 first).  Errors: INVALID_ARG (NULL or misaligned pointers, fx_rows == fy_rows),
+ * NOT_BUILT, UNSUPPORTED (plan off the FP32 network path, bad world or rank), CUDA. */
+tdg_status tdg_slab_rows_forward(tdg_plan p, int world, int rank, const void* sigma_rows, void* z_rows,
+                                 tdg_stream stream);
+tdg_status tdg_slab_unpack_z(tdg_plan p, int world, int rank, const void* recv, void* z_cols, tdg_stream stream);
+tdg_status tdg_slab_columns(tdg_plan p, int world, int rank, const void* z_cols, void* g_cols, tdg_stream stream);
+tdg_status tdg_slab_pack_g(tdg_plan p, int world, int rank, const void* g_cols, void* send, tdg_stream stream);
+tdg_status tdg_slab_rows_inverse(tdg_plan p, int world, int rank, const void* g_rows, void* fx_rows,
+                                 void* fy_rows, tdg_stream stream);
+
 /* Transform lengths chosen for the plan: the padded periods px, py (even, 2^a 3^b,
  * >= 2n - 1) along x and y.  Any out pointer may be NULL. */
 tdg_status tdg_plan_info(const tdg_plan p, int* px, int* py, int* order, int* precision);
 
 /* Kernel path a forward solve of this plan runs: 0 = generic (any size, FP64 and FP32;
- * full spectra), 1 = register-transform path with two exchanges per transform (the
- * FP32_TC16 form; sides of 1024, 2048 or 4096 cells; half spectra), 2 = FP32 one-barrier
- * transform network with TMA tile movement (sides of 1024, 2048 or 4096 cells; half
- * spectra in the network's order).  Valid after tdg_build_kernel_tables; -1 for a NULL
- * plan. */
+ * full spectra), 2 = FP32 one-barrier transform network (sides that are multiples of 16
+ * from 128 to 4096 cells; half spectra in the network's order), 3 = the same network with
+ * the column pass's DFT_16 stages on the tensor cores (the FP32_TC16 form).  Valid after
+ * tdg_build_kernel_tables; -1 for a NULL plan. */
 int tdg_plan_path(const tdg_plan p);
 
 /* Release everything the plan owns (synchronises its device first). */

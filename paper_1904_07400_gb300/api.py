@@ -91,7 +91,8 @@ class Plan:
         return {"px": px.value, "py": py.value, "order": order.value, "precision": prec.value}
 
     def path(self) -> int:
-        """0: generic kernels, 1: FP32 register-transform kernels."""
+        """0: generic kernels, 2: FP32 transform network, 3: the network with the column pass
+        on the tensor cores (FP32_TC16)."""
         return int(native.load().tdg_plan_path(self._h))
 
     def workspace_bytes(self) -> int:

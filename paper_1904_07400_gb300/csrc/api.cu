@@ -172,10 +172,10 @@ tdg_status ensure_workspace(Plan& p) {
 }
 
 // the tensor-core form runs on the register-transform kernels: sides of 1024, 2048, 4096
-bool tc16_available(int nx, int ny) {
-    auto ok = [](int n) { return n == 1024 || n == 2048 || n == 4096; };
-    return ok(nx) && ok(ny);
-}
+// FP32_TC16 runs the network path with its column pass on the tensor cores: sides that the
+// network takes, columns (x) of a transform length of 2048 or 4096 (two warp groups of 128
+// rows, or one, per product)
+bool tc16_available(int nx, int ny) { return net_fp32_length(nx) >= 2048 && net_fp32_length(ny) != 0; }
 
 }  // namespace
 
@@ -209,7 +209,7 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
     if (order < 1 || order > 5 || nx < 1 || ny < 1) return TDG_ERR_INVALID_ARG;
     if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy) || !isfinite(G)) return TDG_ERR_INVALID_ARG;
     if (prec != TDG_FP64 && prec != TDG_FP32 && prec != TDG_FP32_TC16) return TDG_ERR_INVALID_ARG;
-    if (prec == TDG_FP32_TC16 && (!tc16_available(nx, ny) || order > 3)) return TDG_ERR_UNSUPPORTED;
+    if (prec == TDG_FP32_TC16 && !tc16_available(nx, ny)) return TDG_ERR_UNSUPPORTED;
     if (device < 0) return TDG_ERR_INVALID_ARG;
     if (nx > kMaxN || ny > kMaxN) return TDG_ERR_UNSUPPORTED;
     tdg_plan_s* h = new (std::nothrow) tdg_plan_s();
@@ -227,7 +227,7 @@ tdg_status tdg_init(tdg_plan* out, int nx, int ny, int order, double dx, double 
     // FP32 grids whose sides are multiples of 16 from 128 to 4096 cells run the transform
     // network, whose lengths are 512 .. 4096: pad to twice that length (any padded period
     // of at least 2n - 1 gives the same cropped result)
-    const bool net = prec == TDG_FP32 && net_fp32_length(nx) && net_fp32_length(ny);
+    const bool net = (prec == TDG_FP32 || prec == TDG_FP32_TC16) && net_fp32_length(nx) && net_fp32_length(ny);
     p.ax = make_axis(nx, net ? net_fp32_length(nx) : 0);
     p.ay = make_axis(ny, net ? net_fp32_length(ny) : 0);
     p.hy = p.ay.P / 2 + 1;
@@ -324,14 +324,10 @@ static tdg_status build_plan(tdg_plan h, const double* wx_host, const double* wy
     else
         TDG_TRY(launch_spectra<float>(p, placed_x, placed_y, scratch, reinterpret_cast<float*>(p.spec), s));
     if (net_fp32_eligible(p)) {
-        // FP32: one-barrier network kernels, spectra in the network's order
+        // FP32 and FP32_TC16: one-barrier network kernels, spectra in the network's order
         TDG_TRY(cudaMalloc(&p.spec_half, net_fp32_spec_bytes(p)));
         TDG_TRY(cudaMalloc(&p.net_tw, net_fp32_table_bytes(p)));
         TDG_TRY(launch_net_tables(p, s));
-    } else if (fast_fp32_eligible(p)) {
-        // FP32_TC16: two-exchange register kernels
-        TDG_TRY(cudaMalloc(&p.spec_half, fast_fp32_spec_bytes(p)));
-        TDG_TRY(launch_half_spectra(p, s));
     }
     TDG_TRY(cudaStreamSynchronize(s));
     cudaFree(placed_x);
@@ -612,8 +608,8 @@ tdg_status tdg_plan_info(const tdg_plan h, int* px, int* py, int* order, int* pr
 
 int tdg_plan_path(const tdg_plan h) {
     if (!h) return -1;
-    if (h->p.spec_half && h->p.net_tw) return 2;
-    return (h->p.spec_half && fast_fp32_eligible(h->p)) ? 1 : 0;
+    if (h->p.spec_half && h->p.net_tw) return h->p.prec == TDG_FP32_TC16 ? 3 : 2;
+    return 0;
 }
 
 tdg_status tdg_destroy(tdg_plan h) {

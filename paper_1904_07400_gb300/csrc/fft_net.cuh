@@ -123,11 +123,21 @@ __device__ __forceinline__ void stage_factors(const Bases& bs, cf* f2, cf* f3) {
     tw3(f3, bs.b3);
 }
 
+// butterfly providers of the network: stage<R>(v) runs the radix-R butterflies of one stage
+// on the thread's 16 values (R = 16: one DFT_16).  The default runs them on the FP32 pipes;
+// a kernel may pass another provider (e.g. DFT_16 as tensor-core products).
+struct CoreDft {
+    template <int R>
+    __device__ __forceinline__ void stage(cf* v) {
+        reg::butterflies<R>(v);
+    }
+};
+
 // forward DFT, NS in, SP out
-template <int L, typename TW>
-__device__ __forceinline__ void fwd_p(cf* v, cf* buf, const TW& tw, int t) {
+template <int L, typename TW, typename DF = CoreDft>
+__device__ __forceinline__ void fwd_p(cf* v, cf* buf, const TW& tw, int t, DF&& df = DF{}) {
     constexpr int R = Cfg<L>::R, NM = Cfg<L>::NM;
-    reg::dft16(v);
+    df.template stage<16>(v);
 #pragma unroll
     for (int kc = 0; kc < 16; ++kc) buf[(kc % R) * 272 + (kc / R) * 16 * R + t] = v[kc];
     __syncthreads();
@@ -138,7 +148,7 @@ __device__ __forceinline__ void fwd_p(cf* v, cf* buf, const TW& tw, int t) {
 #pragma unroll
         for (int b = 0; b < R; ++b) v[m * R + b] = slab[m * 16 * R + b * 16 + a];
     tw.apply2(v);
-    reg::butterflies<R>(v);
+    df.template stage<R>(v);
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < 16; ++s) slab[s * 17 + a] = v[s];
@@ -146,7 +156,7 @@ __device__ __forceinline__ void fwd_p(cf* v, cf* buf, const TW& tw, int t) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = slab[a * 17 + i];
     tw.apply3(v);
-    reg::dft16(v);
+    df.template stage<16>(v);
 }
 
 template <int L>
@@ -156,10 +166,10 @@ __device__ __forceinline__ void fwd(cf* v, cf* buf, const Bases& bs, int t) {
 
 // transposed network, SP in, NS out (forward kernels): the unnormalised inverse DFT is
 // conj(inv_t(conj(X)))
-template <int L, typename TW>
-__device__ __forceinline__ void inv_t_p(cf* v, cf* buf, const TW& tw, int t) {
+template <int L, typename TW, typename DF = CoreDft>
+__device__ __forceinline__ void inv_t_p(cf* v, cf* buf, const TW& tw, int t, DF&& df = DF{}) {
     constexpr int R = Cfg<L>::R, NM = Cfg<L>::NM;
-    reg::dft16(v);
+    df.template stage<16>(v);
     tw.apply3(v);
     const int a = t & 15;
     cf* slab = buf + (t >> 4) * 272;
@@ -169,7 +179,7 @@ __device__ __forceinline__ void inv_t_p(cf* v, cf* buf, const TW& tw, int t) {
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = slab[s * 17 + a];
-    reg::butterflies<R>(v);
+    df.template stage<R>(v);
     tw.apply2(v);
     __syncwarp();
 #pragma unroll
@@ -179,7 +189,7 @@ __device__ __forceinline__ void inv_t_p(cf* v, cf* buf, const TW& tw, int t) {
     __syncthreads();
 #pragma unroll
     for (int kc = 0; kc < 16; ++kc) v[kc] = buf[(kc % R) * 272 + (kc / R) * 16 * R + t];
-    reg::dft16(v);
+    df.template stage<16>(v);
 }
 
 template <int L>

@@ -1,17 +1,8 @@
-// Register-resident FFT of one line of length L = 16 * R1 * 16 (R1 in {4, 8, 16}) by T =
-// L / 16 threads, 16 complex values per thread, two exchanges through padded shared memory.
-//
-// Data distribution at entry and exit: thread t holds element t + r * T in v[r], r < 16
-// ("natural strided").  Three Stockham stages (radix 16, R1, 16); the last stage leaves its
-// outputs exactly where the first stage of the next transform reads its inputs, so a
-// forward transform, a pointwise product and an inverse transform chain without any
-// reordering.  The inverse transform is conj(FFT(conj(x))).
-//
-// Shared buffer per line: L + L/16 complex values; element i lives at i + i/16 (the pad
-// spreads the stride-16 stores of the first stage over all banks).
+// Register butterflies and twiddle helpers of the transform network (fft_net.cuh): radix
+// 2, 4, 8 and 16 DFTs on a thread's 16 complex values, powers of a twiddle base, the
+// per-element twist W_2L^(t + r T) of the padded column transform, and the padded
+// shared-memory index.
 #pragma once
-
-#include <cuda_fp16.h>
 
 #include "tdg_internal.cuh"
 
@@ -108,121 +99,11 @@ __device__ __forceinline__ void dft16(cf* a) {
     t = a[11]; a[11] = a[14]; a[14] = t;
 }
 
-// ---------------------------------------------------------------------------------------
-// Tensor-core DFT_16 (the TC16 form): the 32 butterflies of a warp as one real product
-//   [Yr; Yi] = [[C, S], [-S, C]] [Xr; Xi],  C = cos(2 pi r k / 16), S = sin(2 pi r k / 16)
-// on mma.sync.m16n8k16 (FP16 operands, FP32 accumulation).  Operands are split into
-// FP16 hi + lo parts and three products are accumulated (hi.hi + hi.lo + lo.hi), after a
-// power-of-two scale that brings the warp's largest value near 1.
-// ---------------------------------------------------------------------------------------
-struct TcConst {
-    unsigned c_hi[4], c_lo[4], s_hi[4], s_lo[4], n_hi[4], n_lo[4];  // A fragments of C, S, -S
-};
-
-__device__ __forceinline__ unsigned pack_h2(float a, float b) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<unsigned*>(&h);
-}
-
-__device__ __forceinline__ void split_h2(float a, float b, unsigned& hi, unsigned& lo) {
-    __half2 h = __floats2half2_rn(a, b);
-    float2 f = __half22float2(h);
-    __half2 l = __floats2half2_rn(a - f.x, b - f.y);
-    hi = *reinterpret_cast<unsigned*>(&h);
-    lo = *reinterpret_cast<unsigned*>(&l);
-}
-
-// A fragments (row-major 16 x 16) of this lane for the DFT_16 matrices
-__device__ __forceinline__ TcConst make_tc_const(int lane) {
-    TcConst k;
-    const int g = lane >> 2, q = lane & 3;
-    const int rows[4] = {g, g + 8, g, g + 8};
-    const int cols[4] = {2 * q, 2 * q, 2 * q + 8, 2 * q + 8};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float c[2], sn[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            int rk = (rows[i] * (cols[i] + e)) & 15;
-            sincospif((float)rk / 8.0f, &sn[e], &c[e]);
-        }
-        split_h2(c[0], c[1], k.c_hi[i], k.c_lo[i]);
-        split_h2(sn[0], sn[1], k.s_hi[i], k.s_lo[i]);
-        split_h2(-sn[0], -sn[1], k.n_hi[i], k.n_lo[i]);
-    }
-    return k;
-}
-
-__device__ __forceinline__ void mma16816(float* d, const unsigned* a, unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-constexpr int kTcRow = 17;  // complex values per butterfly row of the warp scratch (16 + pad)
-constexpr int kTcWarpScratch = 32 * kTcRow;
-
-// DFT_16 of this thread's butterfly v[0..15]; ws: this warp's scratch (kTcWarpScratch)
-__device__ __forceinline__ void dft16_tc(cf* v, cf* ws, const TcConst& K) {
-    const int lane = threadIdx.x & 31;
-    const int g = lane >> 2, q = lane & 3;
-    float m = 0.f;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        ws[lane * kTcRow + r] = v[r];
-        m = fmaxf(m, fmaxf(fabsf(v[r].x), fabsf(v[r].y)));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    // scale = 2^-e with 2^(e-1) <= m < 2^e: scaled values below 1
-    int e = m > 0.f ? ((__float_as_int(m) >> 23) & 255) - 126 : 0;
-    const float sc = __int_as_float((127 - e) << 23), inv = __int_as_float((127 + e) << 23);
-    __syncwarp();
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int n = nt * 8 + g;  // butterfly (column) of this lane's B fragment
-        const cf x0 = ws[n * kTcRow + 2 * q], x1 = ws[n * kTcRow + 2 * q + 1];
-        const cf x8 = ws[n * kTcRow + 2 * q + 8], x9 = ws[n * kTcRow + 2 * q + 9];
-        unsigned rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
-        split_h2(x0.x * sc, x1.x * sc, rh0, rl0);
-        split_h2(x8.x * sc, x9.x * sc, rh1, rl1);
-        split_h2(x0.y * sc, x1.y * sc, ih0, il0);
-        split_h2(x8.y * sc, x9.y * sc, ih1, il1);
-        float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
-        mma16816(yr, K.c_hi, rh0, rh1);
-        mma16816(yr, K.c_hi, rl0, rl1);
-        mma16816(yr, K.c_lo, rh0, rh1);
-        mma16816(yr, K.s_hi, ih0, ih1);
-        mma16816(yr, K.s_hi, il0, il1);
-        mma16816(yr, K.s_lo, ih0, ih1);
-        mma16816(yi, K.n_hi, rh0, rh1);
-        mma16816(yi, K.n_hi, rl0, rl1);
-        mma16816(yi, K.n_lo, rh0, rh1);
-        mma16816(yi, K.c_hi, ih0, ih1);
-        mma16816(yi, K.c_hi, il0, il1);
-        mma16816(yi, K.c_lo, ih0, ih1);
-        __syncwarp();  // every lane has read this tile's inputs
-        const int n0 = nt * 8 + 2 * q;  // output columns n0, n0 + 1; rows g and g + 8
-        ws[n0 * kTcRow + g] = mk(yr[0] * inv, yi[0] * inv);
-        ws[(n0 + 1) * kTcRow + g] = mk(yr[1] * inv, yi[1] * inv);
-        ws[n0 * kTcRow + g + 8] = mk(yr[2] * inv, yi[2] * inv);
-        ws[(n0 + 1) * kTcRow + g + 8] = mk(yr[3] * inv, yi[3] * inv);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = ws[lane * kTcRow + r];
-    __syncwarp();
-}
-
 // radix-R butterflies of one stage on the thread's 16 values; butterfly b uses
 // v[b * R .. b * R + R - 1] (element r at v[b * R + r])
-template <int R, bool TC = false>
-__device__ __forceinline__ void butterflies(cf* v, cf* ws = nullptr, const TcConst* K = nullptr) {
-    if constexpr (R == 16 && TC) {
-        dft16_tc(v, ws, *K);
-    } else if constexpr (R == 16) {
+template <int R>
+__device__ __forceinline__ void butterflies(cf* v) {
+    if constexpr (R == 16) {
         dft16(v);
     } else if constexpr (R == 8) {
         dft8<1>(v);
@@ -236,30 +117,6 @@ __device__ __forceinline__ void butterflies(cf* v, cf* ws = nullptr, const TcCon
         dft4(v[8], v[9], v[10], v[11]);
         dft4(v[12], v[13], v[14], v[15]);
     }
-}
-
-// One exchange: registers (outputs of a stage of radix RA with stride NSA) -> shared ->
-// registers (inputs of the next stage of radix RB).  tw: W_L^m at tw[m * TS].
-template <int L, int RA, int NSA, int RB>
-__device__ __forceinline__ void exchange(cf* v, cf* buf, int t) {
-    constexpr int T = L / 16;
-    constexpr int BA = 16 / RA;
-#pragma unroll
-    for (int b = 0; b < BA; ++b) {
-        int j = t + T * b;
-        int base = (j / NSA) * NSA * RA + (j % NSA);
-#pragma unroll
-        for (int r = 0; r < RA; ++r) buf[pad(base + r * NSA)] = v[b * RA + r];
-    }
-    __syncthreads();
-    constexpr int BB = 16 / RB;
-#pragma unroll
-    for (int b = 0; b < BB; ++b) {
-        int j = t + T * b;
-#pragma unroll
-        for (int r = 0; r < RB; ++r) v[b * RB + r] = buf[pad(j + r * (L / RB))];
-    }
-    __syncthreads();
 }
 
 // exp(-2 pi i r / 32), r < 32: the factors W_2L^(r T) = W_32^r of the per-element twists
@@ -337,34 +194,6 @@ __device__ __forceinline__ void apply_powers(cf* v, cf w1, cf w4, cf w8) {
     }
 }
 
-// Twiddle bases of one thread, loaded once per kernel and reused by every transform the
-// thread runs (they depend only on t): for the middle stage (radix R1, NS = 16) and the
-// last stage (radix 16, NS = L/16) the table entries W^e, W^4e, W^8e of each butterfly.
-template <int L, int R1>
-struct TwBase {
-    static constexpr int B1 = 16 / R1;
-    cf m1[B1], m4[B1], m8[B1];
-    cf l1, l4, l8;
-};
-
-template <int L, int R1, int TS>
-__device__ __forceinline__ TwBase<L, R1> load_tw_base(const cf* tw, int t) {
-    constexpr int T = L / 16;
-    constexpr int STEP1 = L / (16 * R1);
-    TwBase<L, R1> b;
-#pragma unroll
-    for (int q = 0; q < TwBase<L, R1>::B1; ++q) {
-        const int e = ((t + T * q) % 16) * STEP1;
-        b.m1[q] = ld_tw(tw, e * TS);
-        b.m4[q] = R1 > 4 ? ld_tw(tw, ((4 * e) % L) * TS) : b.m1[q];
-        b.m8[q] = R1 > 8 ? ld_tw(tw, ((8 * e) % L) * TS) : b.m1[q];
-    }
-    b.l1 = ld_tw(tw, t * TS);
-    b.l4 = ld_tw(tw, ((4 * t) % L) * TS);
-    b.l8 = ld_tw(tw, ((8 * t) % L) * TS);
-    return b;
-}
-
 // W_2L^(t + r T) for r < 16, from the table entry W_2L^t (tw has W_2L^m at tw[m]) and the
 // constants W_2L^(r T) = W_32^r (T = L / 16)
 __device__ __forceinline__ cf twist(cf wt, int r) { return cmul(wt, w32(r)); }
@@ -373,39 +202,6 @@ __device__ __forceinline__ cf twist(cf wt, int r) { return cmul(wt, w32(r)); }
 // from a different table entry than twist() on purpose: the compiler cannot merge the two,
 // so the factors are not kept alive across the transforms in between.
 __device__ __forceinline__ cf untwist(cf wtc, int r) { return cmulc(wtc, w32(r)); }
-
-// Forward FFT of length L = 16 * R1 * 16; v natural strided in and out.  buf: this line's
-// shared buffer (L + L/16 values).  tb: the thread's twiddle bases (load_tw_base).
-// With TC, every radix-16 stage runs on the tensor cores (ws: the warp's scratch, K: the
-// lane's DFT_16 fragments); other radices stay on the FP32 pipes.
-template <int L, int R1, bool TC = false>
-__device__ __forceinline__ void fft(cf* v, cf* buf, const TwBase<L, R1>& tb, int t, cf* ws = nullptr,
-                                    const TcConst* K = nullptr) {
-    static_assert(16 * R1 * 16 == L, "L = 16 * R1 * 16");
-    butterflies<16, TC>(v, ws, K);
-    exchange<L, 16, 1, R1>(v, buf, t);
-#pragma unroll
-    for (int q = 0; q < TwBase<L, R1>::B1; ++q) apply_powers<R1>(v + q * R1, tb.m1[q], tb.m4[q], tb.m8[q]);
-    butterflies<R1, TC>(v, ws, K);
-    exchange<L, R1, 16, 16>(v, buf, t);
-    apply_powers<16>(v, tb.l1, tb.l4, tb.l8);
-    butterflies<16, TC>(v, ws, K);
-}
-
-template <int L, int R1, bool TC = false>
-__device__ __forceinline__ void ifft(cf* v, cf* buf, const TwBase<L, R1>& tb, int t, cf* ws = nullptr,
-                                     const TcConst* K = nullptr) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
-    fft<L, R1, TC>(v, buf, tb, t, ws, K);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = conjg(v[r]);
-}
-
-template <int L> struct Mid;
-template <> struct Mid<1024> { static constexpr int R1 = 4; };
-template <> struct Mid<2048> { static constexpr int R1 = 8; };
-template <> struct Mid<4096> { static constexpr int R1 = 16; };
 
 }  // namespace reg
 }  // namespace tdg

@@ -32,7 +32,12 @@ namespace {
 using net::cf;
 using reg::pad;
 
-constexpr int kTW = 2;  // tile width of the intermediates
+// Tile widths (complex values per row of a tile) of the intermediates.  Row passes move
+// one tile cell per tile, so wider tiles mean fewer, larger cells for them, while the column
+// pass's stores then touch more cache lines per warp; measured at 4096^2, widening G to
+// four columns saved pass C 10 us and cost pass B 52 us, so both stay at two.
+constexpr int kTW = 2;  // Z (pass A -> pass B) and the adjoint's intermediates
+constexpr int kGW = 2;  // G_x, G_y (pass B -> pass C)
 
 
 // ---------------------------------------------------------------------------------------
@@ -350,6 +355,9 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// generic-proxy shared-memory writes become visible to the async proxy (TMA, tensor core)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void flag_error(int* err, int code) {
     if (err) atomicCAS(err, 0, code);
 }
@@ -416,6 +424,125 @@ __device__ __forceinline__ void tmem_load16(unsigned a, cf* v) {
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// 16 values (16 columns) at a; no wait
+__device__ __forceinline__ void tmem_store16f_nowait(unsigned a, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(a),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+        "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------------------
+// DFT_16 as tensor-core products (the FP32_TC16 form's column pass).  The 16 complex values
+// of each thread form one row of A (32 reals: Re x_r, Im x_r at 2 r, 2 r + 1); the forward
+// DFT_16 in real form is B (K = 32 inputs x N = 32 outputs); D = A B lands in tensor memory.
+// Operands are TF32 (tcgen05.mma kind::tf32, FP32 accumulation), each split into hi + lo:
+// hi keeps the top 10 mantissa bits (exact in TF32), lo = x - hi, and three products
+// A_hi B_hi + A_lo B_hi + A_hi B_lo keep the error near FP32's (the dropped lo lo term is
+// below 2^-20 of the product).  A warp group (128 threads, lanes 0..127) shares one product:
+// its threads store their rows, meet at a named barrier, one thread issues the twelve MMAs
+// (K = 8 each) and commits them to the group's mbarrier, and every thread reads its row of
+// D back.  Tensor memory of a group (column c0): A_hi [c0, +32), A_lo [+32, +64),
+// D [+64, +96).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// instruction descriptor: D F32, A and B TF32, both K-major, M = 128, N = 32
+constexpr unsigned kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// shared-memory descriptor of a K-major operand without swizzle: core matrices of 8 rows x
+// 16 bytes, LBO = byte step between core matrices along K, SBO = along N
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_tf32_ts(unsigned d, unsigned a, unsigned long long bdesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %4, p;\n}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(acc), "r"(kTcIdesc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// B of the forward DFT_16 in real form, as the kernels stage it in shared memory: element
+// (k, n) (input real k = 2 r + part, output real n = 2 q + part) at float offset
+// (n / 8) 256 + (k / 4) 32 + (n % 8) 4 + k % 4 (K-major core matrices: LBO 128 B, SBO 1024 B);
+// hi at [0, 1024), lo at [1024, 2048)
+constexpr int kTcBFloats = 2048;
+__global__ void k_tc_bmat(float* __restrict__ b) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 1024) return;
+    const int k = e >> 5, n = e & 31;
+    const int r = k >> 1, kp = k & 1, q = n >> 1, np = n & 1;
+    double sn, cs;
+    sincospi(-2.0 * (double)((r * q) & 15) / 16.0, &sn, &cs);  // W_16^(r q) = cs + i sn
+    // y_q = sum_r W_16^(r q) x_r: Re y = cs Re x - sn Im x, Im y = sn Re x + cs Im x
+    const double w = np == 0 ? (kp == 0 ? cs : -sn) : (kp == 0 ? sn : cs);
+    const float hi = tf32_hi((float)w);
+    const int off = (n >> 3) * 256 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+    b[off] = hi;
+    b[1024 + off] = (float)(w - (double)hi);
+}
+
+struct TcDft {
+    unsigned arow;  // this thread's lane at the group's A_hi column (A_lo + 32, D + 64)
+    unsigned a0;    // lane 0 of the group at its A_hi column (the MMA operands)
+    unsigned bhi;   // shared address of B hi (B lo at + 4096)
+    unsigned long long* bar;  // the group's mbarrier
+    int* err;
+    int g;          // warp group (named barrier 1 + g)
+    bool leader;    // the group's thread that issues the MMAs
+    unsigned ph;    // phase of the group's next mbarrier completion
+
+    template <int R>
+    __device__ __forceinline__ void stage(cf* v) {
+        if constexpr (R != 16) {
+            reg::butterflies<R>(v);
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float hi[16], lo[16];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const cf x = v[8 * h + i];
+                    hi[2 * i] = tf32_hi(x.x);
+                    hi[2 * i + 1] = tf32_hi(x.y);
+                    lo[2 * i] = x.x - hi[2 * i];
+                    lo[2 * i + 1] = x.y - hi[2 * i + 1];
+                }
+                tmem_store16f_nowait(arow + 16 * h, hi);
+                tmem_store16f_nowait(arow + 32 + 16 * h, lo);
+            }
+            tmem_wait_st();
+            tmem_fence_before();
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+            if (leader) {
+                tmem_fence_after();
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) mma_tf32_ts(a0 + 64, a0 + 8 * ks, smem_desc(bhi + 256 * ks, 128, 1024), ks);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_tf32_ts(a0 + 64, a0 + 32 + 8 * ks, smem_desc(bhi + 256 * ks, 128, 1024), 1);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_tf32_ts(a0 + 64, a0 + 8 * ks, smem_desc(bhi + 4096 + 256 * ks, 128, 1024), 1);
+                mma_commit(bar);
+            }
+            if (!mbar_wait(bar, ph)) flag_error(err, TDG_ERR_TIMEOUT);
+            ph ^= 1u;
+            tmem_fence_after();
+            tmem_load16(arow + 64, v);
+        }
+    }
+};
 
 // ---------------------------------------------------------------------------------------
 // Tables
@@ -570,8 +697,8 @@ __global__ void __launch_bounds__(L / 16, 3)
 }
 
 // ---------------------------------------------------------------------------------------
-// pass C: rows i of one component at a time.  A row's L/2 tile cells arrive by TMA, its
-// Nyquist cell by a plain load.  Shared memory: S = the row (L + 2 complex values),
+// pass C: rows i of one component at a time.  A row's L/kGW tile cells arrive by TMA, its
+// Nyquist value by a plain load.  Shared memory: S = the row (L + 2 complex values),
 // E = network buffer, bar = the row's mbarrier.
 // ---------------------------------------------------------------------------------------
 template <int L>
@@ -602,11 +729,12 @@ __global__ void __launch_bounds__(L / 16, 3)
     // thread 0: start moving item `it` into S (cells by TMA, the Nyquist cell by hand)
     auto issue = [&](int it) {
         const int i = it % nx, comp = it / nx;
+        constexpr int kB = L / kGW < kBox ? L / kGW : kBox;  // cells per box
         mbar_expect_tx(bar, (unsigned)(L * sizeof(cf)));
 #pragma unroll 1
-        for (int b = 0; b < L / 2 / kBox; ++b) tma_load_4d(S + 2 * b * kBox, &gmap, 0, i, b * kBox, comp, bar);
+        for (int b = 0; b < L / kGW / kB; ++b) tma_load_4d(S + kGW * b * kB, &gmap, 0, i, b * kB, comp, bar);
         const cf* g = comp ? g1 : g0;
-        S[L] = ld2(g + (size_t)(L / 2) * nx * kTW + (size_t)i * kTW);  // read back by thread 0 only
+        S[L] = ld2(g + (size_t)(L / kGW) * nx * kGW + (size_t)i * kGW);  // read back by thread 0 only
     };
     if (t == 0) mbar_init(bar, 1);
     __syncthreads();
@@ -727,9 +855,9 @@ struct Stash {
     }
 };
 
-template <int L, int H>
+template <int L, int H, typename ST>
 __device__ __forceinline__ void spec_products(cf* v, const float2* __restrict__ sh, int t, int pt, int tm,
-                                              const Stash<L>& ys) {
+                                              const ST& ys) {
     constexpr int T = L / 16;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
@@ -785,7 +913,7 @@ constexpr int cols_min_blocks() {
 template <int L, int ORD>
 __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
     k_net_cols(const cf* __restrict__ z, int nx, int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
-               const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy) {
+               const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy, int ky0) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     constexpr int HS = L / 2 + 2;
@@ -803,8 +931,9 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
     if constexpr (kTm) {
         if (t < 32) tmem_alloc(tslot, kCols);
     }
-    const int ky = blockIdx.x;
-    const int tile = ky >> 1, c = ky & 1;
+    // column ky0 + b of the spectra; Z, G_x, G_y hold the columns from ky0 on (ky0 even)
+    const int kl = blockIdx.x, ky = ky0 + kl;
+    const int tile = kl >> 1, c = kl & 1;
     const size_t slab = (size_t)nx * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
     const float2* se = spec + (size_t)ky * 2 * HS;
@@ -896,12 +1025,12 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
     // G = conj(u_even + W_2L^n u_odd); W_2L^n as conj of W_2L^-n (table entry 2L - t);
     // rows past the grid are not stored
     const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
-    cf* gxc = gx + (size_t)tile * slab + c;
-    cf* gyc = gy + (size_t)tile * slab + c;
+    cf* gxc = gx + (size_t)(kl / kGW) * nx * kGW + kl % kGW;
+    cf* gyc = gy + (size_t)(kl / kGW) * nx * kGW + kl % kGW;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int n = t + r * T;
-        if (n < nx) gxc[(size_t)n * kTW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+        if (n < nx) gxc[(size_t)n * kGW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
     }
     sB.load16(v);
     __syncthreads();
@@ -914,7 +1043,7 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
         for (int e = 0; e < 4; ++e) {
             const int r = 4 * g + e;
             const int n = t + r * T;
-            if (n < nx) gyc[(size_t)n * kTW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
+            if (n < nx) gyc[(size_t)n * kGW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
         }
     }
     if constexpr (kTm) {
@@ -923,6 +1052,154 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
         tmem_fence_after();
         if (t < 32) tmem_dealloc(*tslot, kCols);
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// pass B of the FP32_TC16 form (columns of 2048 or 4096 cells): k_net_cols with every
+// DFT_16 of the network as tensor-core products (TcDft).  Tensor memory per warp group:
+// A_hi, A_lo, D and stash slot B (32 columns each, 128 a group); stash slot A lives in shared
+// memory, and the twiddle powers are formed at every stage (tensor memory is full).
+// ---------------------------------------------------------------------------------------
+template <int L>
+constexpr size_t tc_cols_bmat_offset() {  // bytes: E, xb, edge, tensor slot and mbarriers, aligned
+    constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
+    return (((size_t)(2 * BUF) * sizeof(cf) + 4 * (T / 32) * sizeof(cf) + 32 + 1023) / 1024) * 1024;
+}
+template <int L>
+constexpr size_t tc_cols_smem_bytes() {
+    return tc_cols_bmat_offset<L>() + kTcBFloats * sizeof(float) + (size_t)16 * (L / 16) * sizeof(cf);
+}
+
+template <int L, int ORD>
+__global__ void __launch_bounds__(L / 16, 2)
+    k_net_cols_tc(const cf* __restrict__ z, int nx, int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
+                  const float2* __restrict__ spec, const float* __restrict__ bmat, cf* __restrict__ gx,
+                  cf* __restrict__ gy, int* __restrict__ err) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    constexpr int HS = L / 2 + 2;
+    constexpr unsigned kCols = T;  // 128 columns per warp group
+    static_assert(T == 128 || T == 256, "columns of 2048 or 4096 cells");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
+    cf* xb = E + BUF;                         // the column (padded natural), later the even x result
+    cf* edge = xb + BUF;
+    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 4 * (T / 32));
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tslot + 4);  // one per warp group
+    float* bsm = reinterpret_cast<float*>(smem_raw + tc_cols_bmat_offset<L>());
+    cf* sslot = reinterpret_cast<cf*>(bsm + kTcBFloats);  // stash slot A, [r][t]
+    const int t = threadIdx.x;
+    if (t < 32) tmem_alloc(tslot, kCols);
+    if (t == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+    }
+    // B (hi, lo) into shared memory, seen by the tensor core's proxy after the barrier below
+    for (int i = t; i < kTcBFloats / 4; i += T)
+        reinterpret_cast<float4*>(bsm)[i] = __ldg(reinterpret_cast<const float4*>(bmat) + i);
+    fence_async_smem();
+    const int ky = blockIdx.x;
+    const int tile = ky >> 1, c = ky & 1;
+    const size_t slab = (size_t)nx * kTW;
+    const cf* zc = z + (size_t)tile * slab + c;
+    const float2* se = spec + (size_t)ky * 2 * HS;
+    const float2* so = se + HS;
+    if (t == 0) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(se), "r"((unsigned)(2 * HS * sizeof(float2)))
+                     : "memory");
+    }
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    const int nact = nx >> 4;
+    cf v[16];
+    const bool solve = ORD < 0 ? ord != 0 : ORD != 0;
+    if (solve) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)  // row 16 t + r sits at r (nx / 16) + t
+            v[r] = t < nact ? ld2(zc + (size_t)(r * nact + t) * kTW) : mk(0.f, 0.f);
+        if constexpr (ORD < 0)
+            solve_chunk<cf>(v, t, nact, T, edge, ord);
+        else if constexpr (ORD != 0)
+            solve_chunk_o<ORD, cf>(v, t, nact, T, edge);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[pad(16 * t + r)] = v[r];
+        tmem_fence_before();
+        __syncthreads();  // also publishes the tensor-memory address, the mbarriers and B
+        tmem_fence_after();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = xb[pad(t + r * T)];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            v[r] = n < nx ? ld2(zc + (size_t)n * kTW) : mk(0.f, 0.f);
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+    }
+    const int g = t >> 7;
+    const unsigned gcol = *tslot + 128u * (unsigned)g;
+    const unsigned arow = gcol + ((unsigned)(32 * ((t >> 5) & 3)) << 16);
+    TcDft df{arow, gcol, smem_u32(bsm), bars + g, err, g, (t & 127) == 0, 0u};
+    const Stash<L, false> sA{0u, sslot, t};
+    const Stash<L, true> sB{arow + 96, nullptr, t};
+    const net::GenTw<L> gt{bs};
+    auto FWD = [&](cf* vv) { net::fwd_p<L>(vv, E, gt, t, df); };
+    auto INV = [&](cf* vv) { net::inv_t_p<L>(vv, E, gt, t, df); };
+    const int pt = net::perm<L>(t);
+    const int te = pt == 0 ? 0 : net::perm_inv<L>(T - pt);  // even half: mirror of k is L - k
+    const int to = net::perm_inv<L>(T - 1 - pt);             // odd half: mirror of k is L - 1 - k
+    {
+        const cf wt = reg::ld_tw(tw, t);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cf y[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) y[e] = cmul(v[4 * q + e], reg::twist(wt, 4 * q + e));
+            sB.store4(q, y);
+        }
+        sB.store_done();
+    }
+    FWD(v);
+    spec_products<L, 0>(v, se, t, pt, te, sA);
+    INV(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) xb[pad(t + r * T)] = v[r];  // even x result, own slots
+    sA.load16(v);
+    __syncthreads();
+    INV(v);
+    sA.store16(v);  // even y result
+    sB.load16(v);   // x W_2L^n
+    __syncthreads();
+    FWD(v);
+    spec_products<L, 1>(v, so, t, pt, to, sB);
+    INV(v);
+    const cf wtc = reg::ld_tw(tw, (2 * L - t) & (2 * L - 1));
+    cf* gxc = gx + (size_t)(ky / kGW) * nx * kGW + ky % kGW;
+    cf* gyc = gy + (size_t)(ky / kGW) * nx * kGW + ky % kGW;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int n = t + r * T;
+        if (n < nx) gxc[(size_t)n * kGW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+    }
+    sB.load16(v);
+    __syncthreads();
+    INV(v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        cf ey[4];
+        sA.load4(q, ey);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 4 * q + e;
+            const int n = t + r * T;
+            if (n < nx) gyc[(size_t)n * kGW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (t < 32) tmem_dealloc(*tslot, kCols);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1227,17 +1504,18 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// the tiled intermediate(s) as a tensor of floats {4 (one tile cell), nx rows, ntile cells,
-// ncomp}: strides 16 B, nx * 16 B, comp_bytes; box {4, 1, kBox, 1}
+// the tiled intermediate(s) as a tensor of floats {2 tw (one tile cell), nx rows, ntile cells,
+// ncomp}: strides 8 tw B, nx * 8 tw B, comp_bytes; box {2 tw, 1, min(kBox, cells), 1}
 cudaError_t encode_tiles(CUtensorMap* map, void* base, int nx, int ntile, int ncomp, size_t comp_bytes,
-                         bool rank4 = false) {
+                         bool rank4 = false, int tw = kTW, int cells = kBox) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const cuuint32_t rank = (ncomp > 1 || rank4) ? 4 : 3;
-    cuuint64_t dims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ntile, (cuuint64_t)ncomp};
-    cuuint64_t strides[3] = {16, (cuuint64_t)nx * 16,
-                             (cuuint64_t)(comp_bytes ? comp_bytes : (size_t)ntile * nx * 16)};
-    cuuint32_t box[4] = {4, 1, (cuuint32_t)kBox, 1};
+    const cuuint64_t cell = (cuuint64_t)tw * 8;
+    cuuint64_t dims[4] = {(cuuint64_t)(2 * tw), (cuuint64_t)nx, (cuuint64_t)ntile, (cuuint64_t)ncomp};
+    cuuint64_t strides[3] = {cell, (cuuint64_t)nx * cell,
+                             (cuuint64_t)(comp_bytes ? comp_bytes : (size_t)ntile * nx * cell)};
+    cuuint32_t box[4] = {(cuuint32_t)(2 * tw), 1, (cuuint32_t)std::min(kBox, cells), 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1266,20 +1544,27 @@ int len_x(const Plan& p) { return p.ax.P / 2; }
 int len_y(const Plan& p) { return p.ay.P / 2; }
 const cf* bases_x(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw); }
 const cf* bases_y(const Plan& p) { return reinterpret_cast<const cf*>(p.net_tw) + len_x(p) / 8; }
+// FP32_TC16 plans: the DFT_16 matrix (k_tc_bmat) after the bases, 256-byte aligned
+size_t tc_bmat_offset(const Plan& p) { return (((size_t)(len_x(p) / 8 + len_y(p) / 8) * sizeof(cf) + 255) / 256) * 256; }
+const float* tc_bmat(const Plan& p) {
+    return reinterpret_cast<const float*>(reinterpret_cast<const char*>(p.net_tw) + tc_bmat_offset(p));
+}
 
 template <int LX, int LY, int ORD>
 cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     const int hy = p.hy;
     const int ntile = (hy + kTW - 1) / kTW;
     const size_t n_el = (size_t)ntile * p.nx * kTW;
+    const int ntile_g = (hy + kGW - 1) / kGW;
+    const size_t n_el_g = (size_t)ntile_g * p.nx * kGW;
     cf* z = reinterpret_cast<cf*>(work);
     cf* gx = z + n_el;
-    cf* gy = gx + n_el;
+    cf* gy = gx + n_el_g;
     const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
     cudaError_t e;
     CUtensorMap gmap;
-    if ((e = encode_tiles(&gmap, gx, p.nx, ntile, 2, n_el * sizeof(cf)))) return e;
+    if ((e = encode_tiles(&gmap, gx, p.nx, ntile_g, 2, n_el_g * sizeof(cf), false, kGW, len_y(p) / kGW))) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
@@ -1296,10 +1581,21 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     k_net_rows<LY, OR><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ord, ord != 0, p.nx, bases_y(p), twy, z);
     if ((e = cudaGetLastError())) return e;
     mark(p, 1, s);
-    sm = cols_smem_bytes<LX>();
-    if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
-    k_net_cols<LX, OC><<<hy, LX / 16, sm, s>>>(z, p.nx, ord, bases_x(p), twx,
-                                           reinterpret_cast<const float2*>(p.spec_half), gx, gy);
+    if constexpr (LX >= 2048) {
+        if (p.prec == TDG_FP32_TC16) {
+            sm = tc_cols_smem_bytes<LX>();
+            if ((e = set_smem(k_net_cols_tc<LX, OC>, sm))) return e;
+            k_net_cols_tc<LX, OC><<<hy, LX / 16, sm, s>>>(z, p.nx, ord, bases_x(p), twx,
+                                                         reinterpret_cast<const float2*>(p.spec_half), tc_bmat(p),
+                                                         gx, gy, p.err);
+        }
+    }
+    if (p.prec != TDG_FP32_TC16) {
+        sm = cols_smem_bytes<LX>();
+        if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
+        k_net_cols<LX, OC><<<hy, LX / 16, sm, s>>>(z, p.nx, ord, bases_x(p), twx,
+                                               reinterpret_cast<const float2*>(p.spec_half), gx, gy, 0);
+    }
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
     sm = inv_bytes<LY>();
@@ -1311,6 +1607,78 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     e = cudaGetLastError();
     mark(p, 3, s);
     return e;
+}
+
+// ---------------------------------------------------------------------------------------
+// Slab decomposition of one grid (the distribution of Sec. 2.3: the solves and transforms
+// split over ranks in slabs, with transposes between them).  A rank's passes are the
+// passes above on its share: pass A on its rows (a grid of `nrows` rows), pass B on its
+// frequency columns ky0 .. (ky0 even), pass C on its rows again.  Layouts: Z row slab
+// [tile][row position], Z column slab [tile - t0][position of all nx rows], G column slab
+// [component][tile - t0][row], G row slab [component][tile][row], cells of two columns.
+// ---------------------------------------------------------------------------------------
+template <int LY, int ORD>
+cudaError_t slab_rows_o(const Plan& p, const float* sigma_rows, int nrows, cf* zr, cudaStream_t s) {
+    constexpr int OR = LY == 4096 ? ORD : -1;
+    const int ord = solve_order(p);
+    const size_t sm = rows_bytes<LY>();
+    cudaError_t e;
+    if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
+    k_net_rows<LY, OR><<<nrows, LY / 16, sm, s>>>(sigma_rows, p.ny, ord, ord != 0, nrows, bases_y(p),
+                                                  reinterpret_cast<const cf*>(p.tw_y), zr);
+    return cudaGetLastError();
+}
+
+template <int LX, int ORD>
+cudaError_t slab_cols_o(const Plan& p, const cf* zc, int ky0, int nky, cf* gxc, cf* gyc, cudaStream_t s) {
+    constexpr int OC = LX == 4096 ? ORD : -1;
+    const size_t sm = cols_smem_bytes<LX>();
+    cudaError_t e;
+    if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
+    k_net_cols<LX, OC><<<nky, LX / 16, sm, s>>>(zc, p.nx, solve_order(p), bases_x(p),
+                                                reinterpret_cast<const cf*>(p.tw_x),
+                                                reinterpret_cast<const float2*>(p.spec_half), gxc, gyc, ky0);
+    return cudaGetLastError();
+}
+
+template <int LY>
+cudaError_t slab_rows_inv_l(const Plan& p, const cf* gr, int nrows, float* fx, float* fy, cudaStream_t s) {
+    const int ntile = (p.hy + kGW - 1) / kGW;
+    const size_t n_el = (size_t)ntile * nrows * kGW;
+    cudaError_t e;
+    CUtensorMap gmap;
+    if ((e = encode_tiles(&gmap, const_cast<cf*>(gr), nrows, ntile, 2, n_el * sizeof(cf), false, kGW, LY / kGW)))
+        return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    const size_t sm = inv_bytes<LY>();
+    if ((e = set_smem(k_net_rows_inv<LY>, sm))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
+    const int grid = std::min(2 * nrows, std::max(1, per_sm) * nsm);
+    k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, gr, gr + n_el, nrows, p.ny, bases_y(p),
+                                                 reinterpret_cast<const cf*>(p.tw_y), fx, fy, p.err);
+    return cudaGetLastError();
+}
+
+template <int LY>
+cudaError_t slab_rows_l(const Plan& p, const float* sigma_rows, int nrows, cf* zr, cudaStream_t s) {
+    switch (solve_order(p)) {
+        case 3: return slab_rows_o<LY, 3>(p, sigma_rows, nrows, zr, s);
+        case 4: return slab_rows_o<LY, 4>(p, sigma_rows, nrows, zr, s);
+        case 5: return slab_rows_o<LY, 5>(p, sigma_rows, nrows, zr, s);
+        default: return slab_rows_o<LY, 0>(p, sigma_rows, nrows, zr, s);
+    }
+}
+
+template <int LX>
+cudaError_t slab_cols_l(const Plan& p, const cf* zc, int ky0, int nky, cf* gxc, cf* gyc, cudaStream_t s) {
+    switch (solve_order(p)) {
+        case 3: return slab_cols_o<LX, 3>(p, zc, ky0, nky, gxc, gyc, s);
+        case 4: return slab_cols_o<LX, 4>(p, zc, ky0, nky, gxc, gyc, s);
+        case 5: return slab_cols_o<LX, 5>(p, zc, ky0, nky, gxc, gyc, s);
+        default: return slab_cols_o<LX, 0>(p, zc, ky0, nky, gxc, gyc, s);
+    }
 }
 
 template <int LX, int LY>
@@ -1420,11 +1788,15 @@ int net_fp32_length(int n) {
 }
 
 bool net_fp32_eligible(const Plan& p) {
-    return p.prec == TDG_FP32 && net_fp32_length(p.nx) == len_x(p) && net_fp32_length(p.ny) == len_y(p) &&
+    return (p.prec == TDG_FP32 || (p.prec == TDG_FP32_TC16 && len_x(p) >= 2048)) &&
+           net_fp32_length(p.nx) == len_x(p) && net_fp32_length(p.ny) == len_y(p) &&
            encode_fn() != nullptr;
 }
 
-size_t net_fp32_table_bytes(const Plan& p) { return (size_t)(len_x(p) / 8 + len_y(p) / 8) * sizeof(cf); }
+size_t net_fp32_table_bytes(const Plan& p) {
+    return p.prec == TDG_FP32_TC16 ? tc_bmat_offset(p) + kTcBFloats * sizeof(float)
+                                   : (size_t)(len_x(p) / 8 + len_y(p) / 8) * sizeof(cf);
+}
 
 size_t net_fp32_spec_bytes(const Plan& p) { return (size_t)p.hy * 2 * (len_x(p) / 2 + 2) * sizeof(float2); }
 
@@ -1433,6 +1805,10 @@ cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
     cf* tab = reinterpret_cast<cf*>(p.net_tw);
     if ((e = build_bases(tab, len_x(p), s))) return e;
     if ((e = build_bases(tab + len_x(p) / 8, len_y(p), s))) return e;
+    if (p.prec == TDG_FP32_TC16) {
+        k_tc_bmat<<<4, 256, 0, s>>>(const_cast<float*>(tc_bmat(p)));
+        if ((e = cudaGetLastError())) return e;
+    }
     switch (len_x(p)) {
         case 512: return spectra_axis<512>(p, s);
         case 1024: return spectra_axis<1024>(p, s);
@@ -1448,6 +1824,38 @@ cudaError_t launch_adjoint_net(const Plan& p, const float* gx, const float* gy, 
         case 1024: return run_net_adj_x<1024>(p, gx, gy, gsig, work, s);
         case 2048: return run_net_adj_x<2048>(p, gx, gy, gsig, work, s);
         default: return run_net_adj_x<4096>(p, gx, gy, gsig, work, s);
+    }
+}
+
+cudaError_t launch_slab_rows(const Plan& p, const float* sigma_rows, int nrows, void* zr, cudaStream_t s) {
+    cf* z = reinterpret_cast<cf*>(zr);
+    switch (len_y(p)) {
+        case 512: return slab_rows_l<512>(p, sigma_rows, nrows, z, s);
+        case 1024: return slab_rows_l<1024>(p, sigma_rows, nrows, z, s);
+        case 2048: return slab_rows_l<2048>(p, sigma_rows, nrows, z, s);
+        default: return slab_rows_l<4096>(p, sigma_rows, nrows, z, s);
+    }
+}
+
+cudaError_t launch_slab_cols(const Plan& p, const void* zc, int ky0, int nky, int ntiles, void* gc, cudaStream_t s) {
+    const cf* z = reinterpret_cast<const cf*>(zc);
+    cf* gx = reinterpret_cast<cf*>(gc);
+    cf* gy = gx + (size_t)ntiles * p.nx * kGW;
+    switch (len_x(p)) {
+        case 512: return slab_cols_l<512>(p, z, ky0, nky, gx, gy, s);
+        case 1024: return slab_cols_l<1024>(p, z, ky0, nky, gx, gy, s);
+        case 2048: return slab_cols_l<2048>(p, z, ky0, nky, gx, gy, s);
+        default: return slab_cols_l<4096>(p, z, ky0, nky, gx, gy, s);
+    }
+}
+
+cudaError_t launch_slab_rows_inv(const Plan& p, const void* gr, int nrows, float* fx, float* fy, cudaStream_t s) {
+    const cf* g = reinterpret_cast<const cf*>(gr);
+    switch (len_y(p)) {
+        case 512: return slab_rows_inv_l<512>(p, g, nrows, fx, fy, s);
+        case 1024: return slab_rows_inv_l<1024>(p, g, nrows, fx, fy, s);
+        case 2048: return slab_rows_inv_l<2048>(p, g, nrows, fx, fy, s);
+        default: return slab_rows_inv_l<4096>(p, g, nrows, fx, fy, s);
     }
 }
 

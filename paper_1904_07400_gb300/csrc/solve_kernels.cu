@@ -220,9 +220,8 @@ cudaError_t launch_twiddles(cpx<T>* tw, int P, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* work, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-        // register-resident transforms for sides of 1024, 2048 or 4096 cells
+        // the transform network for sides that are multiples of 16 from 128 to 4096 cells
         if (p.spec_half && p.net_tw) return launch_forward_net(p, sigma, fx, fy, work, s);
-        if (p.spec_half && fast_fp32_eligible(p)) return launch_forward_fast(p, sigma, fx, fy, work, s);
     }
     const Tiled t = tiled_of<T>(p, p.nx);
     const size_t n_el = (size_t)p.ntile * t.slab;

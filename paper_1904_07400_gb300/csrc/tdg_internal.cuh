@@ -129,11 +129,6 @@ cudaError_t launch_spectra(const Plan& p, const double* placed_x, const double* 
 template <typename T>
 cudaError_t launch_forward(const Plan& p, const T* sigma, T* fx, T* fy, void* work,
                            cudaStream_t s);
-bool fast_fp32_eligible(const Plan& p);
-size_t fast_fp32_spec_bytes(const Plan& p);
-cudaError_t launch_half_spectra(const Plan& p, cudaStream_t s);
-cudaError_t launch_forward_fast(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
-                                cudaStream_t s);
 int net_fp32_length(int n);  // FP32 network transform length for a side of n cells, 0: none
 bool net_fp32_eligible(const Plan& p);
 size_t net_fp32_table_bytes(const Plan& p);
@@ -143,6 +138,13 @@ cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, flo
                                cudaStream_t s);
 cudaError_t launch_adjoint_net(const Plan& p, const float* gx, const float* gy, float* gsig, void* work,
                                cudaStream_t s);
+// slab decomposition of one grid (network path): pass A on `nrows` rows into a Z row slab,
+// pass B on columns ky0 .. ky0 + nky - 1 (a column slab of `ntiles` two-column tiles, G_y
+// after G_x), pass C on `nrows` rows of a G row slab (G_y after G_x)
+cudaError_t launch_slab_rows(const Plan& p, const float* sigma_rows, int nrows, void* zr, cudaStream_t s);
+cudaError_t launch_slab_cols(const Plan& p, const void* zc, int ky0, int nky, int ntiles, void* gc, cudaStream_t s);
+cudaError_t launch_slab_rows_inv(const Plan& p, const void* gr, int nrows, float* fx, float* fy, cudaStream_t s);
+constexpr int kSlabCell = 16;  // bytes of one tile cell of the intermediates (two complex floats)
 template <typename T>
 cudaError_t launch_adjoint(const Plan& p, const T* gx, const T* gy, T* gsig, void* work,
                            cudaStream_t s);

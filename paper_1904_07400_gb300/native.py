@@ -52,6 +52,14 @@ SIGNATURES = [
                                        ctypes.POINTER(_c_double)]),
     ("tdg_solve_forces_noalloc", _c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_set_pass_events", _c_int, [_c_void_p, ctypes.POINTER(_c_void_p), _c_int]),
+    ("tdg_slab_partition", _c_int, [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                    ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    ("tdg_slab_bytes", _c_size_t, [_c_void_p, _c_int, _c_int, _c_int]),
+    ("tdg_slab_rows_forward", _c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_void_p]),
+    ("tdg_slab_unpack_z", _c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_void_p]),
+    ("tdg_slab_columns", _c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_void_p]),
+    ("tdg_slab_pack_g", _c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_void_p]),
+    ("tdg_slab_rows_inverse", _c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
     ("tdg_plan_info", _c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     ("tdg_plan_path", _c_int, [_c_void_p]),
@@ -95,7 +103,7 @@ def call(name: str, *args):
     """Call one C entry point; raise TdgError on a non-OK status (status-returning calls)."""
     lib = load()
     res = getattr(lib, name)(*args)
-    if name not in ("tdg_workspace_bytes", "tdg_status_string", "tdg_plan_path"):
+    if name not in ("tdg_workspace_bytes", "tdg_status_string", "tdg_plan_path", "tdg_slab_bytes"):
         check(name, res)
     return res
 

@@ -42,5 +42,11 @@ def test_orders_and_precisions_accepted_at_init(Plan):
             Plan(64, 48, k, 0.1, 0.1, precision=prec, build=False).close()
     with pytest.raises(native.TdgError):
         Plan(64, 48, 6, 0.1, 0.1, precision="fp32", build=False)
+    # FP32_TC16: columns of 2048 or 4096 transform cells (x sides 1040 .. 4096), any order
     with pytest.raises(native.TdgError):
-        Plan(1024, 1024, 4, 0.1, 0.1, precision="fp32_tc16", build=False)
+        Plan(1024, 1024, 3, 0.1, 0.1, precision="fp32_tc16", build=False)
+    with pytest.raises(native.TdgError):
+        Plan(2000, 1000, 3, 0.1, 0.1, precision="fp32_tc16", build=False)  # y side not a multiple of 16
+    for k in (1, 3, 5):
+        Plan(2048, 1024, k, 0.1, 0.1, precision="fp32_tc16", build=False).close()
+        Plan(1040, 128, k, 0.1, 0.1, precision="fp32_tc16", build=False).close()

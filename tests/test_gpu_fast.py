@@ -1,6 +1,7 @@
-"""Parity of the FP32 register-transform path (sides of 1024, 2048, 4096 cells).
+"""Parity of the FP32 and FP32_TC16 forms on the transform-network path (sides that are
+multiples of 16 from 128 to 4096 cells).
 
-The FP32 form of these grids runs the fast kernels; the FP64 form runs the generic ones,
+The FP32 forms of these grids run the network kernels; the FP64 form runs the generic ones,
 so the comparison also cross-checks two independent kernel sets.  Tolerance: FP32
 relative L2 <= 1e-5 against the FP64 oracle (and against the FP64 GPU form, itself within
 1e-12 of the oracle).
@@ -64,11 +65,15 @@ def test_fast_path_edges_and_ragged_support():
     assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
 
 
-@pytest.mark.parametrize("shape,k", [((1024, 1024), 3), ((2048, 1024), 2), ((1024, 4096), 1), ((4096, 4096), 3)])
+@pytest.mark.parametrize("shape,k", [((2048, 1024), 3), ((2048, 2048), 2), ((4096, 1024), 1), ((4096, 4096), 3),
+                                     ((1536, 768), 3), ((2048, 512), 4), ((2048, 512), 5), ((3072, 2000), 3)])
 def test_tc16_form_vs_fp64_gpu(shape, k):
-    # radix-16 stages as split FP16 hi/lo tensor-core products, FP32 accumulation
+    # the column pass's DFT_16 stages as split TF32 hi/lo tensor-core products (tcgen05.mma),
+    # FP32 accumulation; the row passes are the FP32 network kernels
+    from paper_1904_07400_gb300.api import Plan
     nx, ny = shape
     dx, dy = 1.0 / nx, 1.0 / ny
+    assert Plan(nx, ny, k, dx, dy, precision="fp32_tc16").path() == 3
     sigma = syn.clumps(nx, ny, seed=3 + k)
     tc = _forces(nx, ny, k, dx, dy, "fp32_tc16", sigma)
     f64 = _forces(nx, ny, k, dx, dy, "fp64", sigma)
@@ -76,12 +81,30 @@ def test_tc16_form_vs_fp64_gpu(shape, k):
 
 
 def test_tc16_form_vs_oracle():
-    nx, ny = 1024, 2048
-    dx, dy = 1.0 / 1024, 0.5 / 2048
+    nx, ny = 2048, 512
+    dx, dy = 1.0 / 2048, 0.5 / 512
     sigma = syn.clumps(nx, ny, seed=12)
     rx, ry = oracle_solver(nx, ny, 3, dx, dy).forces(sigma)
     tc = _forces(nx, ny, 3, dx, dy, "fp32_tc16", sigma)
     assert rel_l2_pair(*tc, rx, ry) <= TOL_FP32
+
+
+def test_tc16_adjoint_matches_fp64_gpu():
+    # TC16 plans run the FP32 network adjoint
+    import torch
+    from paper_1904_07400_gb300.api import Plan
+    nx, ny = 2048, 1024
+    dx, dy = 1.0 / nx, 1.0 / ny
+    gx, gy = syn.adjoint_weights(nx, ny, 6)
+    out = {}
+    for prec in ("fp32_tc16", "fp64"):
+        p = Plan(nx, ny, 3, dx, dy, precision=prec)
+        t = lambda a: torch.as_tensor(a, dtype=p.dtype, device=p.device)
+        out[prec] = to_np(p.adjoint(t(gx), t(gy)))
+        torch.cuda.synchronize()
+        assert p.device_error() == 0
+    ref = out["fp64"]
+    assert np.linalg.norm(out["fp32_tc16"] - ref) / np.linalg.norm(ref) <= TOL_FP32
 
 
 # sides that are multiples of 16 below the transform length (the plan pads to P = 2L,
