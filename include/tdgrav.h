@@ -232,8 +232,9 @@ tdg_status tdg_set_pass_events(tdg_plan p, void* const* events, int count);
  * tdg_solve_forces, but the scratch is a fixed device array of TDG_NOALLOC_SCRATCH_BYTES
  * that every GPU loading the library holds until the process exits, and the call makes
  * no cudaMalloc, cudaFree or other allocating call.
- *   - The first call on a device looks up that array's device address (once per device,
- *     with the device current); make that first call before any stream capture.
+ *   - The array's device address is looked up when the plan's kernel tables are built
+ *     (tdg_build_kernel_tables, with the plan's device current) and kept in the plan, so
+ *     this call itself makes no set-up call.
  *   - All calls share the one array and it keeps the last call's contents.  Calls that
  *     overlap on the GPU (several streams or host threads) race on it: serialise them.
  * Errors: UNSUPPORTED when tdg_workspace_bytes(p) > TDG_NOALLOC_SCRATCH_BYTES (about

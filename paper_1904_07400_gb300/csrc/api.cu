@@ -330,6 +330,7 @@ static tdg_status build_plan(tdg_plan h, const double* wx_host, const double* wy
         TDG_TRY(launch_net_tables(p, s));
     }
     TDG_TRY(cudaStreamSynchronize(s));
+    if (noalloc_scratch(&p.noalloc) != cudaSuccess) p.noalloc = nullptr;  // set-up of tdg_solve_forces_noalloc
     cudaFree(placed_x);
     cudaFree(placed_y);
     cudaFree(glx);

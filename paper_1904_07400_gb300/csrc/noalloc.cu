@@ -16,8 +16,6 @@
 // caller.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "tdg_internal.cuh"
 
 namespace {
@@ -26,26 +24,16 @@ constexpr size_t kNoallocScratchBytes = TDG_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on `device` (the caller has made it current).  In
-// host code the array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device.
-cudaError_t scratch_address(int device, void** out) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[device]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = ptr;
-    }
-    *out = g_scratch_addr[device];
-    return cudaSuccess;
-}
-
 }  // namespace
+
+namespace tdg {
+// Device address of the scratch array on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address must come from cudaGetSymbolAddress.
+// Called when a plan's kernel tables are built (outside any stream capture), with the plan's
+// device current; the plan keeps the address, so a solve makes no set-up call and a plan
+// never outlives the context it was looked up in.
+cudaError_t noalloc_scratch(void** out) { return cudaGetSymbolAddress(out, g_noalloc_scratch); }
+}  // namespace tdg
 
 extern "C" tdg_status tdg_solve_forces_noalloc(tdg_plan h, const void* sigma, void* fx, void* fy,
                                                tdg_stream stream) {
@@ -57,19 +45,16 @@ extern "C" tdg_status tdg_solve_forces_noalloc(tdg_plan h, const void* sigma, vo
     if (fx == fy || fx == sigma || fy == sigma) return TDG_ERR_INVALID_ARG;
     if (!p.built) return TDG_ERR_NOT_BUILT;
     if (workspace_bytes(p) > kNoallocScratchBytes) return TDG_ERR_UNSUPPORTED;
-    if (p.device < 0 || p.device >= kMaxDevices) return TDG_ERR_UNSUPPORTED;
+    if (!p.noalloc) return TDG_ERR_CUDA;  // the address lookup at build time failed
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (cudaSetDevice(p.device) != cudaSuccess) return TDG_ERR_CUDA;
-    void* scratch = nullptr;
-    cudaError_t e = scratch_address(p.device, &scratch);
-    if (e == cudaSuccess) {
-        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-        if (p.prec == TDG_FP64)
-            e = launch_forward<double>(p, (const double*)sigma, (double*)fx, (double*)fy, scratch, s);
-        else
-            e = launch_forward<float>(p, (const float*)sigma, (float*)fx, (float*)fy, scratch, s);
-    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (p.prec == TDG_FP64)
+        e = launch_forward<double>(p, (const double*)sigma, (double*)fx, (double*)fy, p.noalloc, s);
+    else
+        e = launch_forward<float>(p, (const float*)sigma, (float*)fx, (float*)fy, p.noalloc, s);
     if (prev >= 0) cudaSetDevice(prev);
     return e == cudaSuccess ? TDG_OK : TDG_ERR_CUDA;
 }

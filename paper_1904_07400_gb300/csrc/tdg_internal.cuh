@@ -80,6 +80,7 @@ struct Plan {
     int* err;              // device error word
     double* diag;          // diagnostics: block partials and the six norms (on first use)
     void* spec_phi;        // potential spectrum (-G s_phi / (P_x P_y)), hy x P_x reals, on request
+    void* noalloc;         // device address of the allocation-free solve's scratch array
     int n_ev;              // 0 or 4: events recorded around the passes (instrumentation)
     cudaEvent_t ev[4];
 };
@@ -108,6 +109,7 @@ inline void mark(const Plan& p, int i, cudaStream_t s) {
 }
 
 size_t workspace_bytes(const Plan& p);
+cudaError_t noalloc_scratch(void** out);  // noalloc.cu: the scratch array on the current device
 
 }  // namespace tdg
 

@@ -14,6 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libtdgrav.so")
 
 TDG_OK = 0
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024  # TDG_NOALLOC_SCRATCH_BYTES of include/tdgrav.h
 STATUS = {0: "TDG_OK", 1: "TDG_ERR_INVALID_ARG", 2: "TDG_ERR_UNSUPPORTED", 3: "TDG_ERR_NOT_BUILT",
           4: "TDG_ERR_OOM", 5: "TDG_ERR_CUDA", 6: "TDG_ERR_TIMEOUT", 7: "TDG_ERR_DEVICE_BOUNDS"}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_tc16": 2}

@@ -223,3 +223,12 @@ def test_potential_entry_host_matches_oracle(lib):
             assert abs(got - ref) < 5e-15 * ref
         # even in m and n
         assert native.kernel_entry_host(k, -3, 2, 1.0, 1.0, 2) == native.kernel_entry_host(k, 3, -2, 1.0, 1.0, 2)
+
+
+def test_noalloc_limit_constant_matches_header():
+    import re
+    from paper_1904_07400_gb300 import native
+    hdr = open(os.path.join(ROOT, "include", "tdgrav.h")).read()
+    m = re.search(r"#define TDG_NOALLOC_SCRATCH_BYTES \((\d+)u \* (\d+)u \* (\d+)u\)", hdr)
+    assert m, "TDG_NOALLOC_SCRATCH_BYTES not found"
+    assert int(m.group(1)) * int(m.group(2)) * int(m.group(3)) == native.NOALLOC_SCRATCH_BYTES

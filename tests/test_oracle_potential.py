@@ -33,11 +33,23 @@ def test_potential_far_bands_reach_fp64(k):
         assert abs(got - ref) < 2e-14 * ref, (k, m, n, dy, q)
 
 
+@pytest.mark.slow
+def test_potential_kernel_order5_scale_and_symmetry():
+    """Order 5: w^phi scales with the cell size (4 times for cells four times larger, aspect
+    1:2) and the table is even in m and n, as for orders 1 and 3 (about a minute)."""
+    a = float(kt.w_phi_route(5, 2, 1, 0.25, 0.5, dps=20))
+    b = float(kt.w_phi_route(5, 2, 1, 1.0, 2.0, dps=20))
+    assert abs(4 * a - b) < 1e-14 * b
+    q = kt.potential_table(5, 6, 5, 0.1, 0.1)
+    np.testing.assert_array_equal(q, q[::-1, :])
+    np.testing.assert_array_equal(q, q[:, ::-1])
+
+
 def test_potential_kernel_symmetry_scale_and_moments():
     # proportional to the cell size; even; far away it is the point-mass 1/r with the
     # spline's variance k/12 as the first correction
     for k in (1, 3, 5):
-        if k < 5:  # (order 5 entries are exercised by the direct/FFT and band tests)
+        if k < 5:  # order 5: test_potential_kernel_order5_scale_and_symmetry (slow)
             a = float(kt.w_phi_route(k, 2, 1, 0.25, 0.5, dps=20))
             b = float(kt.w_phi_route(k, 2, 1, 1.0, 2.0, dps=20))
             assert abs(4 * a - b) < 1e-14 * b

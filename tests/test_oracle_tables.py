@@ -255,6 +255,11 @@ def test_near_origin_orders_4_5(k):
     a = kt.w_route_i(k, 2, 1, 0.25, 0.25, dps=20)
     b_ = kt.w_route_i(k, 2, 1, 1.0, 1.0, dps=20)
     assert abs(a - b_) < 1e-17
+    # w is dimensionless: scaling both cell sides by 4 (cells of aspect 1:2) leaves it
+    # unchanged (u r^-3 du dv is scale invariant), to the 40-digit default of route I
+    a = kt.w_route_i(k, 2, 1, 0.25, 0.5)
+    b_ = kt.w_route_i(k, 2, 1, 1.0, 2.0)
+    assert abs(a - b_) < 1e-20
     assert abs(kt.w_route_i(k, 1, 2, 1.0, 1.0, "y") - kt.w_route_i(k, 2, 1, 1.0, 1.0, "x")) < 1e-20
 
 

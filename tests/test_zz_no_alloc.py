@@ -31,11 +31,15 @@ def _noalloc(plan, sigma, fx, fy):
 @pytest.mark.parametrize("shape,k,prec,tol", [((256, 192), 3, "fp32", TOL_FP32),
                                              ((96, 160), 2, "fp64", TOL_FP64),
                                              ((256, 256), 5, "fp32", TOL_FP32),
-                                             ((100, 60), 4, "fp64", TOL_FP64)])
+                                             ((100, 60), 4, "fp64", TOL_FP64),
+                                             ((200, 176), 1, "fp32", TOL_FP32),
+                                             ((1040, 128), 3, "fp32_tc16", TOL_FP32)])
 def test_noalloc_matches_solve_on_two_calls_in_a_row(shape, k, prec, tol):
     import torch
     nx, ny = shape
+    from paper_1904_07400_gb300 import native
     plan = _plan(nx, ny, k, prec)
+    assert plan.workspace_bytes() <= native.NOALLOC_SCRATCH_BYTES
     for call, seed in enumerate((3, 44)):
         s = torch.as_tensor(syn.clumps(nx, ny, seed=seed), dtype=plan.dtype, device=plan.device)
         ref = plan.forces(s)
@@ -53,7 +57,7 @@ def test_noalloc_rejects_plans_beyond_its_scratch():
     from paper_1904_07400_gb300 import native
     lib = library()
     plan = _plan(2048, 2048, 3, "fp32")
-    limit = 32 * 1024 * 1024
+    limit = native.NOALLOC_SCRATCH_BYTES
     assert plan.workspace_bytes() > limit
     s = torch.ones((2048, 2048), dtype=torch.float32, device=plan.device)
     fx = torch.zeros_like(s)
