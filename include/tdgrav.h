@@ -145,14 +145,20 @@ tdg_status tdg_solve_forces_batched(const tdg_plan* plans, int count,
  * paper Sec. 1 motivates such uses): per-grid descriptors, one workspace and dependency
  * counters on the device.  The pointers are captured at creation; the plans must outlive
  * the batch and keep their kernel tables.  Errors: INVALID_ARG (NULL or misaligned
- * pointers, mixed devices), NOT_BUILT, UNSUPPORTED (FP64 or TC16 plans, a grid whose
- * passes do not fit one block), OOM, CUDA. */
+ * pointers, mixed devices), NOT_BUILT, UNSUPPORTED (FP64 or TC16 plans, a grid that fits neither
+ * persistent kernel), OOM, CUDA. */
 tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count,
                             const void* const* sigma, void* const* fx, void* const* fy);
 
-/* Tuning knobs of the persistent kernel (picked by the autotuner): threads per block
- * (256 or 512) and radix preference of the transforms (0: radix 8 first, 1: radix
- * 4).  Errors: INVALID_ARG, UNSUPPORTED (a grid does not fit; the old setting stays). */
+/* Form and knobs of the persistent kernel (picked by the autotuner).  threads 256 or 512:
+ * the generic kernel (any grid that fits one block), with radix preference 0 (radix 8
+ * first) or 1 (radix 4).  threads 64: the kernel on the transform network's item bodies
+ * (every grid FP32 on the network path with sides up to 1024 cells); the second argument
+ * is then the number of units per item (1, 2, 4 or 8; a unit is one row, column or
+ * inverse row of a 1024-length transform, or two of a 512-length one): blocks of 64
+ * threads take the items of the grids in decreasing solve cost, a 1024-length unit on both
+ * warps, a 512-length unit one transform per warp, the column stashes in tensor memory.
+ * Errors: INVALID_ARG, UNSUPPORTED (a grid does not fit; the old setting stays). */
 tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref);
 
 /* Second form of the batch (picked by the autotuner): nstreams > 0 runs each grid's own

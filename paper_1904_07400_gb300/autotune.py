@@ -1,5 +1,6 @@
-"""Autotuner of the batched launch: tries the persistent kernel's knobs (threads per block,
-radix preference of the transforms) and the streams form (each grid's own kernels on 2,
+"""Autotuner of the batched launch: tries the persistent kernels (the one on the transform
+network's item bodies, and the generic one with its threads per block and radix preference
+of the transforms) and the streams form (each grid's own kernels on 2,
 4, 8 or 16 internal streams) on a batch, times each with CUDA events on the current stream,
 keeps the fastest, and caches the choice in a JSON file keyed by the GPU name and the
 batch's grid signature (sizes, orders, precision)."""
@@ -11,7 +12,9 @@ import os
 
 import torch
 
-CANDIDATES = [(512, 0), (512, 1), (256, 0), (256, 1)]
+# (threads, second knob): 64 is the persistent kernel on the network's item bodies with 1, 2,
+# 4 or 8 units per item; 256 and 512 the generic one with radix 8 (0) or radix 4 (1) first
+CANDIDATES = [(64, 1), (64, 2), (64, 4), (64, 8), (512, 0), (512, 1), (256, 0), (256, 1)]
 STREAMS = (2, 4, 8, 16)
 
 

@@ -185,6 +185,13 @@ struct tdg_batch_s {
     cudaEvent_t fork;
     std::vector<int> lane;  // internal stream of each grid (LPT on the solve cost)
     std::vector<int> order; // grids by decreasing cost
+    // persistent kernel on the transform network's item bodies (threads == 64)
+    bool net_ok;            // every grid on the network path with sides up to 1024 cells
+    NetDisk* ndisks;
+    int* nstart;
+    int ntotal;
+    int nblocks;
+    int net_units;          // units per item of the network form
 };
 
 namespace {
@@ -266,8 +273,70 @@ void streams_free(tdg_batch_s* b) {
 // relative cost of one grid's solve: nx ny log2(P_x P_y)
 double solve_cost(const Plan& p) { return (double)p.nx * p.ny * std::log2((double)p.ax.P * p.ay.P); }
 
+// descriptors of the network persistent form, grids in decreasing cost (largest first, so
+// the long items start early and the tail is short); false if a grid is not eligible
+tdg_status net_configure(tdg_batch_s* b) {
+    b->net_ok = false;
+    std::vector<int> ord(b->count);
+    std::vector<double> cost(b->count);
+    for (int d = 0; d < b->count; ++d) {
+        const Plan& p = tdg_plan_internal(b->plans[d]);
+        if (!net_batch_units(p, 0)) return TDG_OK;
+        cost[d] = solve_cost(p);
+        ord[d] = d;
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<NetDisk> host(b->count);
+    std::vector<int> start(kPhases * (b->count + 1), 0);
+    for (int i = 0; i < b->count; ++i) {
+        const int d = ord[i];
+        const Plan& p = tdg_plan_internal(b->plans[d]);
+        NetDisk& g = host[i];
+        memset(&g, 0, sizeof(g));
+        g.sigma = b->sig[d];
+        g.fx = b->fxs[d];
+        g.fy = b->fys[d];
+        const size_t n_el = (size_t)((p.hy + 1) / 2) * p.nx * 2;  // two-column tiles of Z, G_x, G_y
+        g.z = b->wptr[d];
+        g.gx = reinterpret_cast<cpx<float>*>(g.z) + n_el;
+        g.gy = reinterpret_cast<cpx<float>*>(g.gx) + n_el;
+        g.nbx = p.net_tw;
+        g.nby = reinterpret_cast<const cpx<float>*>(p.net_tw) + p.ax.P / 2 / 8;
+        g.twx = p.tw_x;
+        g.twy = p.tw_y;
+        g.spec = p.spec_half;
+        g.nx = p.nx;
+        g.ny = p.ny;
+        g.hy = p.hy;
+        g.ord = solve_order(p);
+        g.lx = p.ax.P / 2;
+        g.ly = p.ay.P / 2;
+        g.uA = net_batch_units(p, 0);
+        g.uB = net_batch_units(p, 1);
+        g.uC = net_batch_units(p, 2);
+        const int U = b->net_units;
+        g.nA = (g.uA + U - 1) / U;
+        g.nB = (g.uB + U - 1) / U;
+        g.nC = (g.uC + U - 1) / U;
+        start[0 * (b->count + 1) + i + 1] = start[0 * (b->count + 1) + i] + g.nA;
+        start[1 * (b->count + 1) + i + 1] = start[1 * (b->count + 1) + i] + g.nB;
+        start[2 * (b->count + 1) + i + 1] = start[2 * (b->count + 1) + i] + g.nC;
+    }
+    int total = 0;
+    for (int ph = 0; ph < kPhases; ++ph) total += start[ph * (b->count + 1) + b->count];
+    cudaError_t e = cudaMemcpy(b->ndisks, host.data(), b->count * sizeof(NetDisk), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->nstart, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = net_batch_blocks(b->device, &b->nblocks);
+    if (e != cudaSuccess) return TDG_ERR_CUDA;
+    b->ntotal = total;
+    b->net_ok = true;
+    return TDG_OK;
+}
+
 void batch_free(tdg_batch_s* b) {
     streams_free(b);
+    cudaFree(b->ndisks);
+    cudaFree(b->nstart);
     cudaFree(b->disks);
     cudaFree(b->start);
     cudaFree(b->done);
@@ -300,6 +369,7 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
     b->withhold = -1;
     b->nstreams = 0;
     b->fork = nullptr;
+    b->net_units = 2;
     b->plans.assign(plans, plans + count);
     b->host.resize(count);
     b->sig.resize(count);
@@ -321,6 +391,8 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
     if (e == cudaSuccess) e = cudaMalloc(&b->done, (kPhases * count + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->ndisks, count * sizeof(NetDisk));
+    if (e == cudaSuccess) e = cudaMalloc(&b->nstart, kPhases * (count + 1) * sizeof(int));
     if (e != cudaSuccess) {
         batch_free(b);
         delete b;
@@ -352,7 +424,15 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
         g.hy = p.hy;
         g.solve = solve_order(p);
     }
-    tdg_status st = batch_configure(b);
+    tdg_status st = net_configure(b);
+    if (st == TDG_OK) {
+        st = batch_configure(b);
+        // grids the generic kernel cannot hold may still run on the network form
+        if (st == TDG_ERR_UNSUPPORTED && b->net_ok) {
+            b->threads = 64;
+            st = TDG_OK;
+        }
+    }
     if (prev >= 0) cudaSetDevice(prev);
     if (st != TDG_OK) {
         batch_free(b);
@@ -364,8 +444,29 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
 }
 
 tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref) {
-    if (!b || (threads != 256 && threads != 512) || radix_pref < 0 || radix_pref > 1)
-        return TDG_ERR_INVALID_ARG;
+    if (!b || (threads != 64 && threads != 256 && threads != 512)) return TDG_ERR_INVALID_ARG;
+    if (threads == 64) {  // the persistent kernel on the network's item bodies; radix_pref: units per item
+        const int u = radix_pref;
+        if (u != 1 && u != 2 && u != 4 && u != 8) return TDG_ERR_INVALID_ARG;
+        if (!b->net_ok) return TDG_ERR_UNSUPPORTED;
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(b->device);
+        const int old_u = b->net_units;
+        b->net_units = u;
+        tdg_status st = net_configure(b);
+        if (st != TDG_OK || !b->net_ok) {
+            b->net_units = old_u;
+            net_configure(b);
+            if (st == TDG_OK) st = TDG_ERR_UNSUPPORTED;
+        } else {
+            b->threads = 64;
+            b->radix_pref = u;
+        }
+        if (prev >= 0) cudaSetDevice(prev);
+        return st;
+    }
+    if (radix_pref < 0 || radix_pref > 1) return TDG_ERR_INVALID_ARG;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
@@ -446,7 +547,31 @@ tdg_status tdg_batch_launch(tdg_batch b, tdg_stream stream) {
         return e == cudaSuccess ? TDG_OK : TDG_ERR_CUDA;
     }
     cudaError_t e = cudaMemsetAsync(b->done, 0, (kPhases * b->count + 1) * sizeof(int), s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && b->threads == 64) {
+        NetBatchDev dv;
+        dv.disks = b->ndisks;
+        dv.start = b->nstart;
+        dv.done = b->done;
+        dv.ticket = b->done + kPhases * b->count;
+        dv.err = b->err;
+        dv.count = b->count;
+        dv.total = b->ntotal;
+        dv.units = b->net_units;
+        // the test hook names a grid in creation order; the network form orders by cost
+        dv.withhold = -1;
+        if (b->withhold >= 0) {
+            std::vector<double> cost(b->count);
+            std::vector<int> ord(b->count);
+            for (int d = 0; d < b->count; ++d) {
+                cost[d] = solve_cost(tdg_plan_internal(b->plans[d]));
+                ord[d] = d;
+            }
+            std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+            for (int i = 0; i < b->count; ++i)
+                if (ord[i] == b->withhold) dv.withhold = i;
+        }
+        e = launch_batched_net(dv, b->nblocks, s);
+    } else if (e == cudaSuccess) {
         BatchDev dv;
         dv.disks = b->disks;
         dv.start = b->start;
@@ -484,9 +609,9 @@ tdg_status tdg_batch_get_error(tdg_batch b) {
 
 tdg_status tdg_batch_info(const tdg_batch b, int* blocks, int* threads, int* items, int* radix_pref) {
     if (!b) return TDG_ERR_INVALID_ARG;
-    if (blocks) *blocks = b->blocks;
+    if (blocks) *blocks = b->threads == 64 ? b->nblocks : b->blocks;
     if (threads) *threads = b->threads;
-    if (items) *items = b->total;
+    if (items) *items = b->threads == 64 ? b->ntotal : b->total;
     if (radix_pref) *radix_pref = b->radix_pref;
     return TDG_OK;
 }

@@ -613,19 +613,18 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // whichever unit issues it, and storing from registers needs neither a staging buffer nor
 // the block to wait for a bulk copy before it exits.
 // ---------------------------------------------------------------------------------------
-// ORD: the order of the row solve (0: none), or -1: the order `ord` given at run time
+// ORD: the order of the row solve (0: none), or -1: the order `ord` given at run time.
+// The body of one row (thread t of the row's T threads, shared memory `smem`), used by
+// k_net_rows and by the batched persistent kernel; row i of sigma, row position i of Z.
 template <int L, int ORD>
-__global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows(const float* __restrict__ sigma, int ny, int ord, int rowmap, int nx, const cf* __restrict__ nb,
-               const cf* __restrict__ tw, cf* __restrict__ z) {
+__device__ __forceinline__ void rows_item(unsigned char* smem, int t, int i, const float* __restrict__ sigma, int ny,
+                                          int ord, int rowmap, int nx, const cf* __restrict__ nb,
+                                          const cf* __restrict__ tw, cf* __restrict__ z) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cf* E = reinterpret_cast<cf*>(smem_raw);
+    cf* E = reinterpret_cast<cf*>(smem);
     cf* U = E + BUF;
     float* edge = reinterpret_cast<float*>(U + BUF);
-    const int t = threadIdx.x;
-    const int i = blockIdx.x;
     const net::Bases bs = net::load_bases<L>(nb, t);
     cf v[16];
     const int nact = ny >> 4;  // threads owning a 16-value chunk of the row
@@ -694,6 +693,14 @@ __global__ void __launch_bounds__(L / 16, 3)
         *reinterpret_cast<float4*>(zr + (size_t)p * nx * kTW) = make_float4(x0.x, x0.y, x1.x, x1.y);
     }
     if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
+}
+
+template <int L, int ORD>
+__global__ void __launch_bounds__(L / 16, 3)
+    k_net_rows(const float* __restrict__ sigma, int ny, int ord, int rowmap, int nx, const cf* __restrict__ nb,
+               const cf* __restrict__ tw, cf* __restrict__ z) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    rows_item<L, ORD>(smem_raw, threadIdx.x, blockIdx.x, sigma, ny, ord, rowmap, nx, nb, tw, z);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -770,6 +777,46 @@ __global__ void __launch_bounds__(L / 16, 3)
             const cf o = E[pad(n)];
             if (2 * n < ny) out[n] = make_float2(o.x, o.y);  // crop to the grid
         }
+    }
+}
+
+// Pass C body for the batched persistent kernel: row i of one component of G (cells of two
+// columns, 16-byte loads into S), then the repack, transform, crop and store of
+// k_net_rows_inv.  Shared memory as k_net_rows_inv (S, then E at inv_e_offset).
+template <int L>
+__device__ __forceinline__ void inv_item(unsigned char* smem, int t, int i, const cf* __restrict__ g, int nx, int ny,
+                                         const cf* __restrict__ nb, const cf* __restrict__ tw, float* __restrict__ f) {
+    constexpr int T = L / 16;
+    cf* S = reinterpret_cast<cf*>(smem);
+    cf* E = reinterpret_cast<cf*>(smem + inv_e_offset<L>());
+    const cf* gr = g + (size_t)i * kGW;
+#pragma unroll
+    for (int q = 0; q < L / 2 / T; ++q) {
+        const int p = t + T * q;
+        *reinterpret_cast<float4*>(S + 2 * p) = __ldg(reinterpret_cast<const float4*>(gr + (size_t)p * nx * kGW));
+    }
+    if (t == 0) S[L] = ld2(gr + (size_t)(L / 2) * nx * kGW);
+    __syncthreads();
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    const cf wt = reg::ld_tw(tw, t);
+    const int pt = net::perm<L>(t);
+    cf v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = t + T * r;
+        v[r] = conjg(pack_c2r(S[k], S[L - k], reg::twist(wt, r)));
+    }
+    net::fwd<L>(v, E, bs, t);
+    __syncthreads();  // every half-warp is done with its slab of E
+#pragma unroll
+    for (int ka = 0; ka < 8; ++ka) E[pad(pt + T * ka)] = conjg(v[ka]);
+    __syncthreads();
+    float2* out = reinterpret_cast<float2*>(f + (size_t)i * ny);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int n = t + T * c;
+        const cf o = E[pad(n)];
+        if (2 * n < ny) out[n] = make_float2(o.x, o.y);
     }
 }
 
@@ -910,29 +957,25 @@ template <int L>
 constexpr int cols_min_blocks() {
     return L == 1024 ? 5 : 2;
 }
-template <int L, int ORD>
-__global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
-    k_net_cols(const cf* __restrict__ z, int nx, int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
-               const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy, int ky0) {
+// The body of one column (thread t of the column's T threads, shared memory `smem`), used by
+// k_net_cols and by the batched persistent kernel: column kl of Z, G_x, G_y (as stored) and
+// ky of the spectra; rows at or past nstore are not stored.  TM: the stashes in tensor
+// memory (its address at *tslot, published to every thread by the body's first barrier).
+template <int L, int ORD, bool TM = (L >= 1024)>
+__device__ __forceinline__ void cols_item(unsigned char* smem, int t, int kl, int ky, const cf* __restrict__ z,
+                                          int nx, int nstore, int ord, const cf* __restrict__ nb,
+                                          const cf* __restrict__ tw, const float2* __restrict__ spec,
+                                          cf* __restrict__ gx, cf* __restrict__ gy, const unsigned* tslot) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     constexpr int HS = L / 2 + 2;
-    constexpr bool kTm = Stash<L>::kTmem;
+    constexpr bool kTm = TM;
     constexpr bool kTwt = cols_twiddles_in_tmem<L>();
     constexpr unsigned kWarpCols = kTwt ? 128 : 64;
-    constexpr unsigned kCols = kTwt ? 256 : (T > 128 ? 128 : 64);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
-    cf* xb = E + BUF;                         // the column (padded natural), later the even x result
+    cf* E = reinterpret_cast<cf*>(smem);  // network buffer
+    cf* xb = E + BUF;                     // the column (padded natural), later the even x result
     cf* edge = xb + BUF;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 4 * (T / 32));
-    cf* sslots = reinterpret_cast<cf*>(tslot + 4);  // shared stash slots A, B (L = 512)
-    const int t = threadIdx.x;
-    if constexpr (kTm) {
-        if (t < 32) tmem_alloc(tslot, kCols);
-    }
-    // column ky0 + b of the spectra; Z, G_x, G_y hold the columns from ky0 on (ky0 even)
-    const int kl = blockIdx.x, ky = ky0 + kl;
+    cf* sslots = reinterpret_cast<cf*>(reinterpret_cast<unsigned*>(edge + 4 * (T / 32)) + 4);  // shared stash slots A, B
     const int tile = kl >> 1, c = kl & 1;
     const size_t slab = (size_t)nx * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
@@ -972,9 +1015,12 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
         __syncthreads();
         tmem_fence_after();
     }
-    const unsigned tA = kTm ? *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + kWarpCols * (unsigned)(t >> 7) : 0u;
-    const Stash<L> sA{tA, sslots, t};
-    const Stash<L> sB{tA + 32, sslots + 16 * T, t};
+    // tensor-memory lanes of this hardware warp (a block may run one column per warp)
+    const unsigned tA = kTm ? *tslot + ((unsigned)(32 * ((threadIdx.x >> 5) & 3)) << 16) +
+                                  kWarpCols * (unsigned)(threadIdx.x >> 7)
+                            : 0u;
+    const Stash<L, kTm> sA{tA, sslots, t};
+    const Stash<L, kTm> sB{tA + 32, sslots + 16 * T, t};
     const TmemTw<L> tt{tA + 64, tA + 96};
     if constexpr (kTwt) {
         cf f[16], g[16];
@@ -1030,7 +1076,7 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int n = t + r * T;
-        if (n < nx) gxc[(size_t)n * kGW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
+        if (n < nstore) gxc[(size_t)n * kGW] = conjg(xb[pad(n)] + cmulc(v[r], reg::untwist(wtc, r)));
     }
     sB.load16(v);
     __syncthreads();
@@ -1043,9 +1089,27 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
         for (int e = 0; e < 4; ++e) {
             const int r = 4 * g + e;
             const int n = t + r * T;
-            if (n < nx) gyc[(size_t)n * kGW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
+            if (n < nstore) gyc[(size_t)n * kGW] = conjg(ey[e] + cmulc(v[r], reg::untwist(wtc, r)));
         }
     }
+}
+
+template <int L, int ORD>
+__global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
+    k_net_cols(const cf* __restrict__ z, int nx, int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
+               const float2* __restrict__ spec, cf* __restrict__ gx, cf* __restrict__ gy, int ky0) {
+    constexpr int T = L / 16;
+    constexpr bool kTm = Stash<L>::kTmem;
+    constexpr unsigned kCols = cols_twiddles_in_tmem<L>() ? 256 : (T > 128 ? 128 : 64);
+    constexpr int BUF = net::Cfg<L>::BUF;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned* tslot = reinterpret_cast<unsigned*>(reinterpret_cast<cf*>(smem_raw) + 2 * BUF + 4 * (T / 32));
+    const int t = threadIdx.x;
+    if constexpr (kTm) {
+        if (t < 32) tmem_alloc(tslot, kCols);
+    }
+    // column ky0 + b of the spectra; Z, G_x, G_y hold the columns from ky0 on (ky0 even)
+    cols_item<L, ORD>(smem_raw, t, blockIdx.x, ky0 + blockIdx.x, z, nx, nx, ord, nb, tw, spec, gx, gy, tslot);
     if constexpr (kTm) {
         tmem_fence_before();
         __syncthreads();
@@ -1483,6 +1547,202 @@ size_t inv_adj_bytes() {
 }
 
 // ---------------------------------------------------------------------------------------
+// The batched persistent kernel on the network item bodies.  Blocks of 64 threads take
+// items in list order from an atomic ticket (every row item of every grid, then every column
+// item, then every inverse-row item); a column item of grid d waits until all of d's row
+// items are finished, an inverse-row item until all its column items are (bounded, about a
+// second, then TDG_ERR_TIMEOUT and the item is skipped).  A 1024-length item runs on both
+// warps; a 512-length item runs one transform per warp (rows 2 j, 2 j + 1, and likewise).
+// The column stashes live in tensor memory: 64 columns a block, warp w on lanes 32 w ...
+// ---------------------------------------------------------------------------------------
+constexpr int kNetBatchThreads = 64;
+constexpr long long kNetSpinLimit = 1000000;  // ~1 s with 1 us naps
+
+template <int L>
+constexpr size_t batch_item_bytes() {  // shared memory of one transform's item, any pass
+    constexpr size_t a = (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(float);
+    constexpr size_t b = (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(cf) + 16;
+    constexpr size_t c = (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf);
+    return ((std::max(a, std::max(b, c)) + 1023) / 1024) * 1024;
+}
+constexpr size_t kNetBatchSmem =
+    batch_item_bytes<1024>() > 2 * batch_item_bytes<512>() ? batch_item_bytes<1024>() : 2 * batch_item_bytes<512>();
+
+__device__ __forceinline__ int find_grid(const int* pref, int count, int item) {
+    int lo = 0, hi = count;  // pref[lo] <= item < pref[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (pref[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kNetBatchMaxGrids = 256;  // grids whose item prefix sums stay in shared memory
+
+// one out-of-line function per item kind, each running the item's units u0 .. u1 - 1: each
+// gets its own register allocation instead of the union of all six in the loop
+__device__ __noinline__ void bitem_rows1024(unsigned char* sm, const NetDisk& g, int u0, int u1) {
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) __syncthreads();  // the previous unit is done with shared memory
+        rows_item<1024, -1>(sm, threadIdx.x, u, g.sigma, g.ny, g.ord, g.ord != 0, g.nx,
+                            reinterpret_cast<const cf*>(g.nby), reinterpret_cast<const cf*>(g.twy),
+                            reinterpret_cast<cf*>(g.z));
+    }
+}
+__device__ __noinline__ void bitem_rows512(unsigned char* sm, const NetDisk& g, int u0, int u1) {
+    const int w = threadIdx.x >> 5;
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) __syncthreads();
+        rows_item<512, -1>(sm + w * batch_item_bytes<512>(), threadIdx.x & 31, 2 * u + w, g.sigma, g.ny, g.ord,
+                           g.ord != 0, g.nx, reinterpret_cast<const cf*>(g.nby), reinterpret_cast<const cf*>(g.twy),
+                           reinterpret_cast<cf*>(g.z));
+    }
+}
+__device__ __noinline__ void bitem_cols1024(unsigned char* sm, const NetDisk& g, int u0, int u1, const unsigned* tm) {
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) {
+            tmem_fence_before();
+            __syncthreads();
+            tmem_fence_after();
+        }
+        cols_item<1024, -1, true>(sm, threadIdx.x, u, u, reinterpret_cast<const cf*>(g.z), g.nx, g.nx, g.ord,
+                                  reinterpret_cast<const cf*>(g.nbx), reinterpret_cast<const cf*>(g.twx),
+                                  reinterpret_cast<const float2*>(g.spec), reinterpret_cast<cf*>(g.gx),
+                                  reinterpret_cast<cf*>(g.gy), tm);
+    }
+}
+__device__ __noinline__ void bitem_cols512(unsigned char* sm, const NetDisk& g, int u0, int u1, const unsigned* tm) {
+    const int w = threadIdx.x >> 5;
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) {
+            tmem_fence_before();
+            __syncthreads();
+            tmem_fence_after();
+        }
+        const int col = 2 * u + w;  // hy is odd: the second warp of the last unit stores nothing
+        const bool real = col < g.hy;
+        const int c = real ? col : g.hy - 1;
+        cols_item<512, -1, true>(sm + w * batch_item_bytes<512>(), threadIdx.x & 31, c, c,
+                                 reinterpret_cast<const cf*>(g.z), g.nx, real ? g.nx : 0, g.ord,
+                                 reinterpret_cast<const cf*>(g.nbx), reinterpret_cast<const cf*>(g.twx),
+                                 reinterpret_cast<const float2*>(g.spec), reinterpret_cast<cf*>(g.gx),
+                                 reinterpret_cast<cf*>(g.gy), tm);
+    }
+}
+__device__ __noinline__ void bitem_inv1024(unsigned char* sm, const NetDisk& g, int u0, int u1) {
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) __syncthreads();
+        const int comp = u / g.nx, i = u - comp * g.nx;
+        inv_item<1024>(sm, threadIdx.x, i, reinterpret_cast<const cf*>(comp ? g.gy : g.gx), g.nx, g.ny,
+                       reinterpret_cast<const cf*>(g.nby), reinterpret_cast<const cf*>(g.twy), comp ? g.fy : g.fx);
+    }
+}
+__device__ __noinline__ void bitem_inv512(unsigned char* sm, const NetDisk& g, int u0, int u1) {
+    const int w = threadIdx.x >> 5;
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) __syncthreads();
+        const int rc = 2 * u + w, comp = rc / g.nx, i = rc - comp * g.nx;
+        inv_item<512>(sm + w * batch_item_bytes<512>(), threadIdx.x & 31, i,
+                      reinterpret_cast<const cf*>(comp ? g.gy : g.gx), g.nx, g.ny, reinterpret_cast<const cf*>(g.nby),
+                      reinterpret_cast<const cf*>(g.twy), comp ? g.fy : g.fx);
+    }
+}
+
+__global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev b) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_item, s_ok;
+    __shared__ unsigned s_tmem;
+    const int t = threadIdx.x;
+    if (t < 32) tmem_alloc(&s_tmem, 64);
+    // the items' prefix sums after the dynamic shared memory, when the batch is small enough
+    const int nstart = 3 * (b.count + 1);
+    int* sstart = reinterpret_cast<int*>(smem_raw + kNetBatchSmem);
+    const bool local = b.count <= kNetBatchMaxGrids;
+    if (local)
+        for (int i = t; i < nstart; i += kNetBatchThreads) sstart[i] = b.start[i];
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const int* st = local ? sstart : b.start;
+    const int* startA = st;
+    const int* startB = st + (b.count + 1);
+    const int* startC = st + 2 * (b.count + 1);
+    const int totA = startA[b.count], totB = startB[b.count];
+    for (;;) {
+        if (t == 0) s_item = atomicAdd(b.ticket, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.total) break;
+        int phase, local_item;
+        const int* pref;
+        if (item < totA) {
+            phase = 0;
+            local_item = item;
+            pref = startA;
+        } else if (item < totA + totB) {
+            phase = 1;
+            local_item = item - totA;
+            pref = startB;
+        } else {
+            phase = 2;
+            local_item = item - totA - totB;
+            pref = startC;
+        }
+        const int d = find_grid(pref, b.count, local_item);
+        const int idx = local_item - pref[d];
+        const NetDisk& g = b.disks[d];
+        if (t == 0) {
+            int ok = 1;
+            if (phase > 0) {
+                const int need = phase == 1 ? g.nA : g.nB;
+                volatile int* cnt = b.done + (phase - 1) * b.count + d;
+                volatile int* errw = b.err;
+                long long spins = 0;
+                while (*cnt < need) {
+                    if (++spins > kNetSpinLimit || *errw != 0) {
+                        ok = 0;
+                        atomicExch(b.err, (int)TDG_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(1000);
+                }
+                __threadfence();
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+            // this item's units: idx * U .. (a unit is one transform of a 1024-length line, two
+            // of a 512-length one)
+            const int units = phase == 0 ? g.uA : (phase == 1 ? g.uB : g.uC);
+            const int u0 = idx * b.units, u1 = min(u0 + b.units, units);
+            if (phase == 0) {
+                if (g.ly == 1024) bitem_rows1024(smem_raw, g, u0, u1);
+                else bitem_rows512(smem_raw, g, u0, u1);
+            } else if (phase == 1) {
+                if (g.lx == 1024) bitem_cols1024(smem_raw, g, u0, u1, &s_tmem);
+                else bitem_cols512(smem_raw, g, u0, u1, &s_tmem);
+            } else {
+                if (g.ly == 1024) bitem_inv1024(smem_raw, g, u0, u1);
+                else bitem_inv512(smem_raw, g, u0, u1);
+            }
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (t == 0) {
+            __threadfence();
+            if (!(phase == 0 && d == b.withhold)) atomicAdd(b.done + phase * b.count + d, 1);
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (t < 32) tmem_dealloc(s_tmem, 64);
+}
+
+// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1857,6 +2117,43 @@ cudaError_t launch_slab_rows_inv(const Plan& p, const void* gr, int nrows, float
         case 2048: return slab_rows_inv_l<2048>(p, g, nrows, fx, fy, s);
         default: return slab_rows_inv_l<4096>(p, g, nrows, fx, fy, s);
     }
+}
+
+int net_batch_units(const Plan& p, int pass) {
+    if (!net_fp32_eligible(p) || p.prec != TDG_FP32 || len_x(p) > 1024 || len_y(p) > 1024) return 0;
+    const int per_y = len_y(p) == 1024 ? 1 : 2, per_x = len_x(p) == 1024 ? 1 : 2;
+    if (pass == 0) return p.nx / per_y;
+    if (pass == 1) return (p.hy + per_x - 1) / per_x;
+    return 2 * p.nx / per_y;
+}
+
+size_t net_batch_smem() { return kNetBatchSmem + 3 * (kNetBatchMaxGrids + 1) * sizeof(int); }
+
+cudaError_t net_batch_blocks(int device, int* blocks) {
+    cudaError_t e;
+    if ((e = set_smem(k_batched_net, net_batch_smem()))) return e;
+    // resident blocks per SM from the kernel's registers (per warp, in units of 256) and
+    // shared memory (plus the 1 KB the driver keeps per block), and 64 of the 512
+    // tensor-memory columns per block
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k_batched_net))) return e;
+    int nsm = 0, regs_sm = 0, smem_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device))) return e;
+    if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device))) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device))) return e;
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (warp_regs * (kNetBatchThreads / 32));
+    const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + net_batch_smem() + 1024);
+    const int per = std::min(std::min(by_regs, by_smem), 8);
+    *blocks = std::max(1, per) * nsm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batched_net(const NetBatchDev& d, int blocks, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = set_smem(k_batched_net, net_batch_smem()))) return e;
+    k_batched_net<<<blocks, kNetBatchThreads, net_batch_smem(), s>>>(d);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,

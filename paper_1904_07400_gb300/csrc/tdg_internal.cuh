@@ -147,6 +147,43 @@ cudaError_t launch_slab_rows(const Plan& p, const float* sigma_rows, int nrows, 
 cudaError_t launch_slab_cols(const Plan& p, const void* zc, int ky0, int nky, int ntiles, void* gc, cudaStream_t s);
 cudaError_t launch_slab_rows_inv(const Plan& p, const void* gr, int nrows, float* fx, float* fy, cudaStream_t s);
 constexpr int kSlabCell = 16;  // bytes of one tile cell of the intermediates (two complex floats)
+
+// One grid of a batch run by the persistent kernel on the transform network's item bodies
+// (sides that are multiples of 16 up to 1024 cells: transform lengths lx, ly of 512 or
+// 1024).  Units per pass: rows (pass A), frequency columns (pass B), rows of one force
+// component (pass C); a 512-length unit holds two of them, one per warp.  An item is a run
+// of consecutive units of one grid and pass.
+struct NetDisk {
+    const float* sigma;
+    float* fx;
+    float* fy;
+    void* z;               // Z, then G_x, G_y in the plan's network workspace layout
+    void* gx;
+    void* gy;
+    const void* nbx;       // network twiddle bases, x axis and y axis
+    const void* nby;
+    const void* twx;       // W_2L tables
+    const void* twy;
+    const void* spec;      // half spectra in network order
+    int nx, ny, hy, ord, lx, ly;
+    int uA, uB, uC;        // units per pass (a unit: one 1024-length transform, two 512-length)
+    int nA, nB, nC;        // items per pass (units grouped by the batch's units per item)
+};
+struct NetBatchDev {
+    const NetDisk* disks;
+    const int* start;      // [3][count + 1] prefix sums of items per pass
+    int* done;             // [3][count] finished items per pass and grid
+    int* ticket;
+    int* err;
+    int count;
+    int total;
+    int withhold;          // grid whose row-pass completions are not counted (test hook), or -1
+    int units;             // units per item
+};
+int net_batch_units(const Plan& p, int pass);  // units of pass 0, 1, 2 for one grid; 0: not eligible
+size_t net_batch_smem();                        // dynamic shared memory of the kernel
+cudaError_t net_batch_blocks(int device, int* blocks);  // one persistent wave
+cudaError_t launch_batched_net(const NetBatchDev& d, int blocks, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adjoint(const Plan& p, const T* gx, const T* gy, T* gsig, void* work,
                            cudaStream_t s);
