@@ -614,12 +614,13 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // the block to wait for a bulk copy before it exits.
 // ---------------------------------------------------------------------------------------
 // ORD: the order of the row solve (0: none), or -1: the order `ord` given at run time.
-// The body of one row (thread t of the row's T threads, shared memory `smem`), used by
-// k_net_rows and by the batched persistent kernel; row i of sigma, row position i of Z.
-template <int L, int ORD>
-__device__ __forceinline__ void rows_item(unsigned char* smem, int t, int i, const float* __restrict__ sigma, int ny,
-                                          int ord, int rowmap, int nx, const cf* __restrict__ nb,
-                                          const cf* __restrict__ tw, cf* __restrict__ z) {
+// The body of one row (thread t of the row's T threads, shared memory `smem`): row i of
+// sigma to its unpacked cells, each handed to sink(q, cell) for p = t + T q; returns
+// X[L] (valid in thread 0).
+template <int L, int ORD, class Sink>
+__device__ __forceinline__ float rows_body(unsigned char* smem, int t, int i, const float* __restrict__ sigma, int ny,
+                                           int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
+                                           Sink&& sink) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     cf* E = reinterpret_cast<cf*>(smem);
@@ -676,10 +677,7 @@ __device__ __forceinline__ void rows_item(unsigned char* smem, int t, int i, con
     for (int ka = 0; ka < 16; ++ka) U[pad(pt + T * ka)] = v[ka];
     const float znyq = v[0].x - v[0].y;  // X[L] (thread 0: v[0] = Z[0])
     __syncthreads();
-    // cells p = t + T q: (X[2p], X[2p+1]) with X[k] = unpack(Z[k], Z[L-k], W_2L^k), stored to
-    // tile p of row position rp
-    const int rp = rowmap ? (i & 15) * (nx >> 4) + (i >> 4) : i;
-    cf* zr = z + (size_t)rp * kTW;
+    // cells p = t + T q: (X[2p], X[2p+1]) with X[k] = unpack(Z[k], Z[L-k], W_2L^k)
     const cf w2t = reg::ld_tw(tw, 2 * t);  // W_2L^(2t)
     const cf w1 = reg::ld_tw(tw, 1);       // W_2L
 #pragma unroll
@@ -690,8 +688,30 @@ __device__ __forceinline__ void rows_item(unsigned char* smem, int t, int i, con
         const cf wk1 = cmul(wk0, w1);
         const cf x0 = unpack_r2c(U[pad(k0)], U[pad((L - k0) & (L - 1))], wk0);
         const cf x1 = unpack_r2c(U[pad(k0 + 1)], U[pad(L - k0 - 1)], wk1);
-        *reinterpret_cast<float4*>(zr + (size_t)p * nx * kTW) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        sink(q, make_float4(x0.x, x0.y, x1.x, x1.y));
     }
+    return znyq;
+}
+
+// Z row position of sigma row i: for solves of order >= 3 row i sits at (i % 16) (nx / 16) +
+// i / 16, so that the column pass's thread t reads its 16-row solve chunk from consecutive
+// positions; otherwise at i
+__device__ __forceinline__ int row_pos(int i, int rowmap, int nx) { return rowmap ? (i & 15) * (nx >> 4) + (i >> 4) : i; }
+__device__ __forceinline__ int pos_row(int rp, int rowmap, int nx) {
+    return rowmap ? 16 * (rp % (nx >> 4)) + rp / (nx >> 4) : rp;
+}
+
+// One row: row i of sigma, its cells stored to tile p of row position row_pos(i) with one
+// 16-byte store each.  Used by k_net_rows and by the batched persistent kernel.
+template <int L, int ORD>
+__device__ __forceinline__ void rows_item(unsigned char* smem, int t, int i, const float* __restrict__ sigma, int ny,
+                                          int ord, int rowmap, int nx, const cf* __restrict__ nb,
+                                          const cf* __restrict__ tw, cf* __restrict__ z) {
+    constexpr int T = L / 16;
+    cf* zr = z + (size_t)row_pos(i, rowmap, nx) * kTW;
+    const float znyq = rows_body<L, ORD>(smem, t, i, sigma, ny, ord, nb, tw, [&](int q, float4 c) {
+        *reinterpret_cast<float4*>(zr + (size_t)(t + T * q) * nx * kTW) = c;
+    });
     if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
 }
 
@@ -701,6 +721,58 @@ __global__ void __launch_bounds__(L / 16, 3)
                const cf* __restrict__ tw, cf* __restrict__ z) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     rows_item<L, ORD>(smem_raw, threadIdx.x, blockIdx.x, sigma, ny, ord, rowmap, nx, nb, tw, z);
+}
+
+__device__ __forceinline__ void st_global_v8(void* p, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+// Pass A on pairs of row positions (2b, 2b + 1), one pair per block: the rows that sit at
+// adjacent positions of Z share every 32-byte sector of Z, so the block transforms both and
+// writes each tile's two cells with one 32-byte store.  The first row's cells wait in tensor
+// memory (32 columns per thread: warp w at lanes 32 (w % 4), columns 32 (w / 4)) while the
+// second row is transformed.  nx even (every side on the network path is a multiple of 16).
+template <int L, int ORD>
+__global__ void __launch_bounds__(L / 16, 3)
+    k_net_rows2(const float* __restrict__ sigma, int ny, int ord, int rowmap, int nx, const cf* __restrict__ nb,
+                const cf* __restrict__ tw, cf* __restrict__ z) {
+    constexpr int T = L / 16;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ unsigned s_tmem;
+    const int t = threadIdx.x;
+    if (t < 32) tmem_alloc(&s_tmem, 64);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned ta = s_tmem + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + 32u * (unsigned)(t >> 7);
+    const int rp = 2 * blockIdx.x;
+    cf* zr = z + (size_t)rp * kTW;
+    // row at position rp: its cells to tensor memory
+    {
+        float4 c0[8];
+        const float znyq = rows_body<L, ORD>(smem_raw, t, pos_row(rp, rowmap, nx), sigma, ny, ord, nb, tw,
+                                             [&](int q, float4 c) { c0[q] = c; });
+        tmem_store16(ta, reinterpret_cast<const cf*>(c0));
+        if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
+    }
+    __syncthreads();  // the first row's reads of the shared buffers are done
+    // row at position rp + 1: each tile's two cells with one store
+    cf c0[16];
+    const float znyq = rows_body<L, ORD>(smem_raw, t, pos_row(rp + 1, rowmap, nx), sigma, ny, ord, nb, tw,
+                                         [&](int q, float4 c) {
+                                             if (q == 0) tmem_load16(ta, c0);
+                                             st_global_v8(zr + (size_t)(t + T * q) * nx * kTW,
+                                                          make_float4(c0[2 * q].x, c0[2 * q].y, c0[2 * q + 1].x,
+                                                                      c0[2 * q + 1].y),
+                                                          c);
+                                         });
+    if (t == 0) zr[(size_t)(L / 2) * nx * kTW + kTW] = mk(znyq, 0.f);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (t < 32) tmem_dealloc(s_tmem, 64);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1810,6 +1882,24 @@ const float* tc_bmat(const Plan& p) {
     return reinterpret_cast<const float*>(reinterpret_cast<const char*>(p.net_tw) + tc_bmat_offset(p));
 }
 
+// Pass A over nx rows: row pairs for the long rows (L >= 2048, a few blocks per SM, 64
+// tensor-memory columns each), one row per block below (up to ten blocks per SM there,
+// more than tensor memory could stash for)
+template <int LY, int OR>
+cudaError_t launch_rows(const float* sigma, int ny, int ord, int nx, const cf* nb, const cf* tw, cf* z,
+                        cudaStream_t s) {
+    const size_t sm = rows_bytes<LY>();
+    cudaError_t e;
+    if constexpr (LY >= 2048) {
+        if ((e = set_smem(k_net_rows2<LY, OR>, sm))) return e;
+        k_net_rows2<LY, OR><<<nx / 2, LY / 16, sm, s>>>(sigma, ny, ord, ord != 0, nx, nb, tw, z);
+    } else {
+        if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
+        k_net_rows<LY, OR><<<nx, LY / 16, sm, s>>>(sigma, ny, ord, ord != 0, nx, nb, tw, z);
+    }
+    return cudaGetLastError();
+}
+
 template <int LX, int LY, int ORD>
 cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     const int hy = p.hy;
@@ -1836,10 +1926,8 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     constexpr int OR = LY == 4096 ? ORD : -1;
     constexpr int OC = LX == 4096 ? ORD : -1;
     const int ord = solve_order(p);
-    if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY, OR><<<p.nx, LY / 16, sm, s>>>(sigma, p.ny, ord, ord != 0, p.nx, bases_y(p), twy, z);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_rows<LY, OR>(sigma, p.ny, ord, p.nx, bases_y(p), twy, z, s))) return e;
     mark(p, 1, s);
     if constexpr (LX >= 2048) {
         if (p.prec == TDG_FP32_TC16) {
@@ -1880,13 +1968,8 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
 template <int LY, int ORD>
 cudaError_t slab_rows_o(const Plan& p, const float* sigma_rows, int nrows, cf* zr, cudaStream_t s) {
     constexpr int OR = LY == 4096 ? ORD : -1;
-    const int ord = solve_order(p);
-    const size_t sm = rows_bytes<LY>();
-    cudaError_t e;
-    if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
-    k_net_rows<LY, OR><<<nrows, LY / 16, sm, s>>>(sigma_rows, p.ny, ord, ord != 0, nrows, bases_y(p),
-                                                  reinterpret_cast<const cf*>(p.tw_y), zr);
-    return cudaGetLastError();
+    return launch_rows<LY, OR>(sigma_rows, p.ny, solve_order(p), nrows, bases_y(p),
+                               reinterpret_cast<const cf*>(p.tw_y), zr, s);
 }
 
 template <int LX, int ORD>
@@ -1969,15 +2052,11 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
-    size_t sm = rows_bytes<LY>();
-    if ((e = set_smem(k_net_rows<LY, 0>, sm))) return e;
     mark(p, 0, s);
-    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gxin, p.ny, 0, 0, p.nx, bases_y(p), twy, zx);
-    if ((e = cudaGetLastError())) return e;
-    k_net_rows<LY, 0><<<p.nx, LY / 16, sm, s>>>(gyin, p.ny, 0, 0, p.nx, bases_y(p), twy, zy);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_rows<LY, 0>(gxin, p.ny, 0, p.nx, bases_y(p), twy, zx, s))) return e;
+    if ((e = launch_rows<LY, 0>(gyin, p.ny, 0, p.nx, bases_y(p), twy, zy, s))) return e;
     mark(p, 1, s);
-    sm = cols_adj_smem_bytes<LX>();
+    size_t sm = cols_adj_smem_bytes<LX>();
     if ((e = set_smem(k_net_cols_adj<LX>, sm))) return e;
     k_net_cols_adj<LX><<<hy, LX / 16, sm, s>>>(zx, zy, p.nx, solve, bases_x(p), twx,
                                                reinterpret_cast<const float2*>(p.spec_half), g);
