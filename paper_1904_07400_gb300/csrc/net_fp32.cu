@@ -852,6 +852,114 @@ __global__ void __launch_bounds__(L / 16, 3)
     }
 }
 
+// Pass C on pairs of rows (2j, 2j + 1) of one component, for the long rows (L >= 2048).
+// Rows 2j and 2j + 1 are adjacent in every tile of G, so one TMA box over the pair view of G
+// (32-byte pieces: both rows' cells of a tile) brings both, with half as many pieces as
+// two single-row loads.  S holds the pair as [tile][row][column] (4 complex per tile) under
+// the TMA's 32-byte swizzle, which exchanges the two 16-byte halves of a tile (the rows)
+// when bit 2 of the tile index is set, and the two Nyquist values at 2L and 2L + 2: value
+// k of row r sits at 4 p + 2 (r ^ (p / 4 % 2)) + k % 2, p = k / 2, for every k <= L.  Without
+// the swizzle, tiles p and p + 4 read by one half-warp would fall in the same banks.  The
+// second row, repacked, waits in tensor memory
+// (32 columns per thread, as in pass A's pairs) while the first is transformed and stored.
+// Persistent over the items w = (component, pair), the next item's load issued as soon as
+// both rows are repacked.
+template <int L>
+constexpr int inv2_e_offset() {
+    return (((2 * L + 4) * 8 + 1023) / 1024) * 1024;  // bytes
+}
+
+template <int L>
+__global__ void __launch_bounds__(L / 16, 2)
+    k_net_rows_inv2(const __grid_constant__ CUtensorMap gmap2, const cf* __restrict__ g0, const cf* __restrict__ g1,
+                    int nx, int ny, const cf* __restrict__ nb, const cf* __restrict__ tw, float* __restrict__ f0,
+                    float* __restrict__ f1, int* __restrict__ err) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    constexpr int kB = L / 2 < kBox ? L / 2 : kBox;  // tiles per box
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    cf* S = reinterpret_cast<cf*>(smem_raw);
+    cf* E = reinterpret_cast<cf*>(smem_raw + inv2_e_offset<L>());
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(E + BUF);
+    unsigned* tslot = reinterpret_cast<unsigned*>(bar + 1);
+    const int t = threadIdx.x;
+    const int npair = nx >> 1;
+    const int nitems = 2 * npair;
+    if ((int)blockIdx.x >= nitems) return;
+    if (t < 32) tmem_alloc(tslot, 64);
+    // thread 0: start moving item `it` into S (both rows' cells by TMA, the Nyquist values by hand)
+    auto issue = [&](int it) {
+        const int j = it % npair, comp = it / npair;
+        mbar_expect_tx(bar, (unsigned)(2 * L * sizeof(cf)));
+#pragma unroll 1
+        for (int b = 0; b < L / 2 / kB; ++b) tma_load_4d(S + 4 * b * kB, &gmap2, 0, j, b * kB, comp, bar);
+        const cf* g = (comp ? g1 : g0) + (size_t)(L / 2) * nx * kGW + (size_t)(2 * j) * kGW;
+        S[2 * L] = ld2(g);  // read back after the next item's barrier
+        S[2 * L + 2] = ld2(g + kGW);
+    };
+    if (t == 0) mbar_init(bar, 1);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned ta = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + 32u * (unsigned)(t >> 7);
+    if (t == 0) issue(blockIdx.x);
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    const cf wt = reg::ld_tw(tw, t);
+    const int pt = net::perm<L>(t);
+    // k = t + T r and its mirror L - k: as T r is a multiple of 16, the tile index moves by
+    // T r / 2 and the swizzle bit and column parity are the thread's own
+    const int sk = (t >> 3) & 1, sm = ((L - t) >> 3) & 1;
+    const cf* Sk = S + 4 * (t >> 1) + (t & 1);
+    const cf* Sm = S + 4 * ((L - t) >> 1) + (t & 1);
+    unsigned ph = 0;
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x, ph ^= 1u) {
+        const int j = w % npair, comp = w / npair;
+        const int ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0);
+        if (!ok) {
+            if (t == 0) flag_error(err, TDG_ERR_TIMEOUT);
+            mbar_wait(bar, ph);  // the load in flight lands before the block leaves
+            break;
+        }
+        cf v[16];
+        // both rows, four values at a time: the first row's to registers, the second row's
+        // to tensor memory
+#pragma unroll
+        for (int r0 = 0; r0 < 16; r0 += 4) {
+            cf u[4];
+#pragma unroll
+            for (int r = r0; r < r0 + 4; ++r) {
+                const cf wr = reg::twist(wt, r);
+                v[r] = conjg(pack_c2r(Sk[2 * T * r + 2 * sk], Sm[-2 * T * r + 2 * sm], wr));
+                u[r - r0] = conjg(pack_c2r(Sk[2 * T * r + 2 * (sk ^ 1)], Sm[-2 * T * r + 2 * (sm ^ 1)], wr));
+            }
+            tmem_store4_nowait(ta + 2 * r0, u);
+        }
+        tmem_wait_st();
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1) tmem_load16(ta, v);
+            net::fwd<L>(v, E, bs, t);  // its barrier: every thread is done with S (h = 0)
+            if (h == 0 && t == 0 && w + (int)gridDim.x < nitems) issue(w + gridDim.x);
+            __syncthreads();  // every half-warp is done with its slab of E
+#pragma unroll
+            for (int ka = 0; ka < 8; ++ka) E[pad(pt + T * ka)] = conjg(v[ka]);
+            __syncthreads();
+            float2* out = reinterpret_cast<float2*>((comp ? f1 : f0) + (size_t)(2 * j + h) * ny);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int n = t + T * c;
+                const cf o = E[pad(n)];
+                if (2 * n < ny) out[n] = make_float2(o.x, o.y);  // crop to the grid
+            }
+            __syncthreads();  // E is read before the next transform writes it
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (t < 32) tmem_dealloc(*tslot, 64);
+}
+
 // Pass C body for the batched persistent kernel: row i of one component of G (cells of two
 // columns, 16-byte loads into S), then the repack, transform, crop and store of
 // k_net_rows_inv.  Shared memory as k_net_rows_inv (S, then E at inv_e_offset).
@@ -1839,7 +1947,8 @@ EncodeTiledFn encode_fn() {
 // the tiled intermediate(s) as a tensor of floats {2 tw (one tile cell), nx rows, ntile cells,
 // ncomp}: strides 8 tw B, nx * 8 tw B, comp_bytes; box {2 tw, 1, min(kBox, cells), 1}
 cudaError_t encode_tiles(CUtensorMap* map, void* base, int nx, int ntile, int ncomp, size_t comp_bytes,
-                         bool rank4 = false, int tw = kTW, int cells = kBox) {
+                         bool rank4 = false, int tw = kTW, int cells = kBox,
+                         CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const cuuint32_t rank = (ncomp > 1 || rank4) ? 4 : 3;
@@ -1850,7 +1959,7 @@ cudaError_t encode_tiles(CUtensorMap* map, void* base, int nx, int ntile, int nc
     cuuint32_t box[4] = {(cuuint32_t)(2 * tw), 1, (cuuint32_t)std::min(kBox, cells), 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -1868,6 +1977,11 @@ size_t rows_bytes() {
 template <int L>
 size_t inv_bytes() {
     return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16;
+}
+
+template <int L>
+size_t inv2_bytes() {
+    return (size_t)inv2_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16;
 }
 
 // transform length of an axis (P / 2) and the plan's bases tables: x axis first (2 T_x
@@ -1900,6 +2014,60 @@ cudaError_t launch_rows(const float* sigma, int ny, int ord, int nx, const cf* n
     return cudaGetLastError();
 }
 
+// Resident blocks per SM of a kernel launched with `threads` threads and `smem` bytes of
+// dynamic shared memory, from its registers (allocated per warp in units of 256) and shared
+// memory (plus the 1 KB the driver keeps per block)
+template <typename K>
+cudaError_t blocks_per_sm(K kernel, int threads, size_t smem, int* per_sm) {
+    cudaError_t e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kernel))) return e;
+    int dev = 0, regs_sm = 0, smem_sm = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev))) return e;
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (warp_regs * ((threads + 31) / 32));
+    const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + smem + 1024);
+    *per_sm = std::max(1, std::min(by_regs, by_smem));
+    return cudaSuccess;
+}
+
+// Pass C over nx rows of both components of G (g0, g1: [tile][row][2], ntile tiles each):
+// persistent, row pairs for the long rows (L >= 2048, two blocks per SM, 64 tensor-memory
+// columns each), single rows below
+template <int LY>
+cudaError_t launch_rows_inv(const cf* g0, const cf* g1, int nx, int ntile, int ny, const cf* nb, const cf* tw,
+                            float* fx, float* fy, int* err, cudaStream_t s) {
+    cudaError_t e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    const size_t comp_bytes = (size_t)(g1 - g0) * sizeof(cf);
+    CUtensorMap gmap;
+    if constexpr (LY >= 2048) {
+        // pair view: cells of 4 complex (rows 2j and 2j + 1 of one tile), nx / 2 pairs
+        // 32-byte pieces under the 32-byte swizzle (the piece is exactly the swizzle span, so
+        // the box's footprint in shared memory is its dense size)
+        if ((e = encode_tiles(&gmap, const_cast<cf*>(g0), nx / 2, ntile, 2, comp_bytes, false, 2 * kGW, LY / kGW,
+                              CU_TENSOR_MAP_SWIZZLE_32B)))
+            return e;
+        const size_t sm = inv2_bytes<LY>();
+        if ((e = set_smem(k_net_rows_inv2<LY>, sm))) return e;
+        if ((e = blocks_per_sm(k_net_rows_inv2<LY>, LY / 16, sm, &per_sm))) return e;
+        const int grid = std::min(nx, std::min(per_sm, 2) * nsm);
+        k_net_rows_inv2<LY><<<grid, LY / 16, sm, s>>>(gmap, g0, g1, nx, ny, nb, tw, fx, fy, err);
+    } else {
+        if ((e = encode_tiles(&gmap, const_cast<cf*>(g0), nx, ntile, 2, comp_bytes, false, kGW, LY / kGW))) return e;
+        const size_t sm = inv_bytes<LY>();
+        if ((e = set_smem(k_net_rows_inv<LY>, sm))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
+        const int grid = std::min(2 * nx, std::max(1, per_sm) * nsm);
+        k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, g0, g1, nx, ny, nb, tw, fx, fy, err);
+    }
+    return cudaGetLastError();
+}
+
 template <int LX, int LY, int ORD>
 cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     const int hy = p.hy;
@@ -1913,13 +2081,7 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     const cf* twx = reinterpret_cast<const cf*>(p.tw_x);
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
     cudaError_t e;
-    CUtensorMap gmap;
-    if ((e = encode_tiles(&gmap, gx, p.nx, ntile_g, 2, n_el_g * sizeof(cf), false, kGW, len_y(p) / kGW))) return e;
-    int dev = 0, nsm = 0;
-    if ((e = cudaGetDevice(&dev))) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
-
-    size_t sm = rows_bytes<LY>();
+    size_t sm;
     // the order is compiled into the 4096-length kernels (pass B issues faster); shorter
     // lengths share one instance for every order (the batched streams form runs many of
     // them side by side, and one instance keeps their code footprint small)
@@ -1946,13 +2108,7 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     }
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
-    sm = inv_bytes<LY>();
-    if ((e = set_smem(k_net_rows_inv<LY>, sm))) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
-    const int grid = std::min(2 * p.nx, std::max(1, per_sm) * nsm);
-    k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, gx, gy, p.nx, p.ny, bases_y(p), twy, fx, fy, p.err);
-    e = cudaGetLastError();
+    e = launch_rows_inv<LY>(gx, gy, p.nx, ntile_g, p.ny, bases_y(p), twy, fx, fy, p.err, s);
     mark(p, 3, s);
     return e;
 }
@@ -1988,20 +2144,8 @@ template <int LY>
 cudaError_t slab_rows_inv_l(const Plan& p, const cf* gr, int nrows, float* fx, float* fy, cudaStream_t s) {
     const int ntile = (p.hy + kGW - 1) / kGW;
     const size_t n_el = (size_t)ntile * nrows * kGW;
-    cudaError_t e;
-    CUtensorMap gmap;
-    if ((e = encode_tiles(&gmap, const_cast<cf*>(gr), nrows, ntile, 2, n_el * sizeof(cf), false, kGW, LY / kGW)))
-        return e;
-    int dev = 0, nsm = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev))) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
-    const size_t sm = inv_bytes<LY>();
-    if ((e = set_smem(k_net_rows_inv<LY>, sm))) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
-    const int grid = std::min(2 * nrows, std::max(1, per_sm) * nsm);
-    k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, gr, gr + n_el, nrows, p.ny, bases_y(p),
-                                                 reinterpret_cast<const cf*>(p.tw_y), fx, fy, p.err);
-    return cudaGetLastError();
+    return launch_rows_inv<LY>(gr, gr + n_el, nrows, ntile, p.ny, bases_y(p), reinterpret_cast<const cf*>(p.tw_y),
+                               fx, fy, p.err, s);
 }
 
 template <int LY>
