@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "fft_net.cuh"
 #include "tdg_internal.cuh"
@@ -616,11 +617,26 @@ __device__ __forceinline__ cf pack_c2r(cf xa, cf xb, cf w) {
 // ORD: the order of the row solve (0: none), or -1: the order `ord` given at run time.
 // The body of one row (thread t of the row's T threads, shared memory `smem`): row i of
 // sigma to its unpacked cells, each handed to sink(q, cell) for p = t + T q; returns
-// X[L] (valid in thread 0).
-template <int L, int ORD, class Sink>
-__device__ __forceinline__ float rows_body(unsigned char* smem, int t, int i, const float* __restrict__ sigma, int ny,
-                                           int ord, const cf* __restrict__ nb, const cf* __restrict__ tw,
-                                           Sink&& sink) {
+// X[L] (valid in thread 0).  A row that is solved comes as the thread's chunk
+// s[16 t .. 16 t + 15] (zeros past the row) from load(x); hook() runs once the row's
+// transform is done with the network buffer E (after a block barrier), before the unpack.
+__device__ __forceinline__ void load_chunk(const float* __restrict__ sigma, int i, int ny, int t, float (&x)[16]) {
+    const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * ny) + 4 * t;
+    const bool in = t < (ny >> 4);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 f = in ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[4 * q] = f.x;
+        x[4 * q + 1] = f.y;
+        x[4 * q + 2] = f.z;
+        x[4 * q + 3] = f.w;
+    }
+}
+
+template <int L, int ORD, class Load, class Hook, class Sink>
+__device__ __forceinline__ float rows_body(unsigned char* smem, int t, int ny, int ord, const cf* __restrict__ nb,
+                                           const cf* __restrict__ tw, const float* __restrict__ row_plain,
+                                           Load&& load, Hook&& hook, Sink&& sink) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     cf* E = reinterpret_cast<cf*>(smem);
@@ -631,17 +647,8 @@ __device__ __forceinline__ float rows_body(unsigned char* smem, int t, int i, co
     const int nact = ny >> 4;  // threads owning a 16-value chunk of the row
     const bool solve = ORD < 0 ? ord != 0 : ORD != 0;
     if (solve) {
-        // thread t owns s[16 t .. 16 t + 15]; past the row: zeros
-        const float4* src = reinterpret_cast<const float4*>(sigma + (size_t)i * ny) + 4 * t;
         float x[16];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 f = t < nact ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            x[4 * q] = f.x;
-            x[4 * q + 1] = f.y;
-            x[4 * q + 2] = f.z;
-            x[4 * q + 3] = f.w;
-        }
+        load(x);
         if constexpr (ORD < 0)
             solve_chunk<float>(x, t, nact, T, edge, ord);
         else if constexpr (ORD != 0)
@@ -660,7 +667,7 @@ __device__ __forceinline__ float rows_body(unsigned char* smem, int t, int i, co
             v[c] = mk(p.x, p.y);
         }
     } else {
-        const float2* row = reinterpret_cast<const float2*>(sigma + (size_t)i * ny);
+        const float2* row = reinterpret_cast<const float2*>(row_plain);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float2 p = 2 * (t + T * c) < ny ? row[t + T * c] : make_float2(0.f, 0.f);
@@ -677,6 +684,7 @@ __device__ __forceinline__ float rows_body(unsigned char* smem, int t, int i, co
     for (int ka = 0; ka < 16; ++ka) U[pad(pt + T * ka)] = v[ka];
     const float znyq = v[0].x - v[0].y;  // X[L] (thread 0: v[0] = Z[0])
     __syncthreads();
+    hook();
     // cells p = t + T q: (X[2p], X[2p+1]) with X[k] = unpack(Z[k], Z[L-k], W_2L^k)
     const cf w2t = reg::ld_tw(tw, 2 * t);  // W_2L^(2t)
     const cf w1 = reg::ld_tw(tw, 1);       // W_2L
@@ -709,9 +717,10 @@ __device__ __forceinline__ void rows_item(unsigned char* smem, int t, int i, con
                                           const cf* __restrict__ tw, cf* __restrict__ z) {
     constexpr int T = L / 16;
     cf* zr = z + (size_t)row_pos(i, rowmap, nx) * kTW;
-    const float znyq = rows_body<L, ORD>(smem, t, i, sigma, ny, ord, nb, tw, [&](int q, float4 c) {
-        *reinterpret_cast<float4*>(zr + (size_t)(t + T * q) * nx * kTW) = c;
-    });
+    const float* row = sigma + (size_t)i * ny;
+    const float znyq = rows_body<L, ORD>(
+        smem, t, ny, ord, nb, tw, row, [&](float(&x)[16]) { load_chunk(sigma, i, ny, t, x); }, [] {},
+        [&](int q, float4 c) { *reinterpret_cast<float4*>(zr + (size_t)(t + T * q) * nx * kTW) = c; });
     if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
 }
 
@@ -734,45 +743,110 @@ __device__ __forceinline__ void st_global_v8(void* p, float4 a, float4 b) {
 // writes each tile's two cells with one 32-byte store.  The first row's cells wait in tensor
 // memory (32 columns per thread: warp w at lanes 32 (w % 4), columns 32 (w / 4)) while the
 // second row is transformed.  nx even (every side on the network path is a multiple of 16).
+//
+// Rows that are solved (order >= 3) and span whole 128-byte pieces (ny % 32 == 0, smap
+// valid: sma != 0) arrive by TMA, one box per row, into the network buffer E under the
+// 128-byte swizzle (the box's inner extent is the swizzle span, so its footprint is the
+// dense row): thread t's chunk is the two halves of piece t / 2, 16-byte unit u of a piece
+// at u ^ (piece % 8), so that the eight threads of a quarter-warp read eight different
+// bank groups.  The first row's load is issued at the start, the second row's as soon as
+// the first row's transform is done with E.  Shared memory: rows_bytes, then the mbarrier
+// and the tensor-memory address.
+template <int L>
+constexpr size_t rows2_bytes() {
+    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(float) + 16;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <int L, int ORD>
 __global__ void __launch_bounds__(L / 16, 3)
-    k_net_rows2(const float* __restrict__ sigma, int ny, int ord, int rowmap, int nx, const cf* __restrict__ nb,
-                const cf* __restrict__ tw, cf* __restrict__ z) {
+    k_net_rows2(const __grid_constant__ CUtensorMap smap, int sma, const float* __restrict__ sigma, int ny, int ord,
+                int rowmap, int nx, const cf* __restrict__ nb, const cf* __restrict__ tw, cf* __restrict__ z,
+                int* __restrict__ err) {
     constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ unsigned s_tmem;
+    unsigned long long* bar =
+        reinterpret_cast<unsigned long long*>(smem_raw + 2 * BUF * sizeof(cf) + 4 * (T / 32) * sizeof(float));
+    unsigned* tslot = reinterpret_cast<unsigned*>(bar + 1);
     const int t = threadIdx.x;
-    if (t < 32) tmem_alloc(&s_tmem, 64);
+    const bool solve = ORD < 0 ? ord != 0 : ORD != 0;
+    const bool tma = solve && sma != 0;
+    const int rp = 2 * blockIdx.x;
+    const int i0 = pos_row(rp, rowmap, nx), i1 = pos_row(rp + 1, rowmap, nx);
+    if (t < 32) tmem_alloc(tslot, 64);
+    if (t == 0 && tma) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (unsigned)(ny * sizeof(float)));
+        tma_load_3d(smem_raw, &smap, 0, 0, i0, bar);
+    }
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    const unsigned ta = s_tmem + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + 32u * (unsigned)(t >> 7);
-    const int rp = 2 * blockIdx.x;
+    const unsigned ta = *tslot + ((unsigned)(32 * ((t >> 5) & 3)) << 16) + 32u * (unsigned)(t >> 7);
     cf* zr = z + (size_t)rp * kTW;
+    unsigned ph = 0;
+    auto load = [&](int i, float(&x)[16]) {
+        if (!tma) {
+            load_chunk(sigma, i, ny, t, x);
+            return;
+        }
+        if (!mbar_wait(bar, ph)) {
+            flag_error(err, TDG_ERR_TIMEOUT);
+            mbar_wait(bar, ph);  // a late copy lands before E is reused
+        }
+        ph ^= 1u;
+        const float4* e = reinterpret_cast<const float4*>(smem_raw) + 8 * (t >> 1);
+        const int sw = (t >> 1) & 7, h = 4 * (t & 1);
+        const bool in = t < (ny >> 4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 f = in ? e[(h + q) ^ sw] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[4 * q] = f.x;
+            x[4 * q + 1] = f.y;
+            x[4 * q + 2] = f.z;
+            x[4 * q + 3] = f.w;
+        }
+    };
     // row at position rp: its cells to tensor memory
     {
         float4 c0[8];
-        const float znyq = rows_body<L, ORD>(smem_raw, t, pos_row(rp, rowmap, nx), sigma, ny, ord, nb, tw,
-                                             [&](int q, float4 c) { c0[q] = c; });
+        const float znyq = rows_body<L, ORD>(
+            smem_raw, t, ny, ord, nb, tw, sigma + (size_t)i0 * ny, [&](float(&x)[16]) { load(i0, x); },
+            [&] {
+                if (t == 0 && tma) {  // E is free: the second row's load
+                    fence_async_smem();
+                    mbar_expect_tx(bar, (unsigned)(ny * sizeof(float)));
+                    tma_load_3d(smem_raw, &smap, 0, 0, i1, bar);
+                }
+            },
+            [&](int q, float4 c) { c0[q] = c; });
         tmem_store16(ta, reinterpret_cast<const cf*>(c0));
         if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
     }
     __syncthreads();  // the first row's reads of the shared buffers are done
     // row at position rp + 1: each tile's two cells with one store
     cf c0[16];
-    const float znyq = rows_body<L, ORD>(smem_raw, t, pos_row(rp + 1, rowmap, nx), sigma, ny, ord, nb, tw,
-                                         [&](int q, float4 c) {
-                                             if (q == 0) tmem_load16(ta, c0);
-                                             st_global_v8(zr + (size_t)(t + T * q) * nx * kTW,
-                                                          make_float4(c0[2 * q].x, c0[2 * q].y, c0[2 * q + 1].x,
-                                                                      c0[2 * q + 1].y),
-                                                          c);
-                                         });
+    const float znyq = rows_body<L, ORD>(
+        smem_raw, t, ny, ord, nb, tw, sigma + (size_t)i1 * ny, [&](float(&x)[16]) { load(i1, x); }, [] {},
+        [&](int q, float4 c) {
+            if (q == 0) tmem_load16(ta, c0);
+            st_global_v8(zr + (size_t)(t + T * q) * nx * kTW,
+                         make_float4(c0[2 * q].x, c0[2 * q].y, c0[2 * q + 1].x, c0[2 * q + 1].y), c);
+        });
     if (t == 0) zr[(size_t)(L / 2) * nx * kTW + kTW] = mk(znyq, 0.f);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    if (t < 32) tmem_dealloc(s_tmem, 64);
+    if (t < 32) tmem_dealloc(*tslot, 64);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2000,13 +2074,33 @@ const float* tc_bmat(const Plan& p) {
 // tensor-memory columns each), one row per block below (up to ten blocks per SM there,
 // more than tensor memory could stash for)
 template <int LY, int OR>
-cudaError_t launch_rows(const float* sigma, int ny, int ord, int nx, const cf* nb, const cf* tw, cf* z,
+cudaError_t launch_rows(const float* sigma, int ny, int ord, int nx, const cf* nb, const cf* tw, cf* z, int* err,
                         cudaStream_t s) {
-    const size_t sm = rows_bytes<LY>();
+    size_t sm = rows_bytes<LY>();
     cudaError_t e;
     if constexpr (LY >= 2048) {
+        // solved rows of whole 128-byte pieces by TMA: a map of sigma as {32 floats, ny / 32
+        // pieces, nx rows}, one row per box, 128-byte swizzle
+        CUtensorMap smap;
+        int sma = 0;
+        if (ord != 0 && ny % 32 == 0 && ((uintptr_t)sigma & 15) == 0) {
+            EncodeTiledFn fn = encode_fn();
+            if (!fn) return cudaErrorNotSupported;
+            cuuint64_t dims[3] = {32, (cuuint64_t)(ny / 32), (cuuint64_t)nx};
+            cuuint64_t strides[2] = {128, (cuuint64_t)ny * sizeof(float)};
+            cuuint32_t box[3] = {32, (cuuint32_t)(ny / 32), 1};
+            cuuint32_t estr[3] = {1, 1, 1};
+            if (fn(&smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(sigma), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+            sma = 1;
+        } else {
+            memset(&smap, 0, sizeof(smap));
+        }
+        sm = rows2_bytes<LY>();
         if ((e = set_smem(k_net_rows2<LY, OR>, sm))) return e;
-        k_net_rows2<LY, OR><<<nx / 2, LY / 16, sm, s>>>(sigma, ny, ord, ord != 0, nx, nb, tw, z);
+        k_net_rows2<LY, OR><<<nx / 2, LY / 16, sm, s>>>(smap, sma, sigma, ny, ord, ord != 0, nx, nb, tw, z, err);
     } else {
         if ((e = set_smem(k_net_rows<LY, OR>, sm))) return e;
         k_net_rows<LY, OR><<<nx, LY / 16, sm, s>>>(sigma, ny, ord, ord != 0, nx, nb, tw, z);
@@ -2089,7 +2183,7 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
     constexpr int OC = LX == 4096 ? ORD : -1;
     const int ord = solve_order(p);
     mark(p, 0, s);
-    if ((e = launch_rows<LY, OR>(sigma, p.ny, ord, p.nx, bases_y(p), twy, z, s))) return e;
+    if ((e = launch_rows<LY, OR>(sigma, p.ny, ord, p.nx, bases_y(p), twy, z, p.err, s))) return e;
     mark(p, 1, s);
     if constexpr (LX >= 2048) {
         if (p.prec == TDG_FP32_TC16) {
@@ -2125,7 +2219,7 @@ template <int LY, int ORD>
 cudaError_t slab_rows_o(const Plan& p, const float* sigma_rows, int nrows, cf* zr, cudaStream_t s) {
     constexpr int OR = LY == 4096 ? ORD : -1;
     return launch_rows<LY, OR>(sigma_rows, p.ny, solve_order(p), nrows, bases_y(p),
-                               reinterpret_cast<const cf*>(p.tw_y), zr, s);
+                               reinterpret_cast<const cf*>(p.tw_y), zr, p.err, s);
 }
 
 template <int LX, int ORD>
@@ -2197,8 +2291,8 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
     mark(p, 0, s);
-    if ((e = launch_rows<LY, 0>(gxin, p.ny, 0, p.nx, bases_y(p), twy, zx, s))) return e;
-    if ((e = launch_rows<LY, 0>(gyin, p.ny, 0, p.nx, bases_y(p), twy, zy, s))) return e;
+    if ((e = launch_rows<LY, 0>(gxin, p.ny, 0, p.nx, bases_y(p), twy, zx, p.err, s))) return e;
+    if ((e = launch_rows<LY, 0>(gyin, p.ny, 0, p.nx, bases_y(p), twy, zy, p.err, s))) return e;
     mark(p, 1, s);
     size_t sm = cols_adj_smem_bytes<LX>();
     if ((e = set_smem(k_net_cols_adj<LX>, sm))) return e;
