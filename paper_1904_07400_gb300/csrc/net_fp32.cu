@@ -1025,7 +1025,9 @@ __global__ void __launch_bounds__(L / 16, 2)
                 const cf o = E[pad(n)];
                 if (2 * n < ny) out[n] = make_float2(o.x, o.y);  // crop to the grid
             }
-            __syncthreads();  // E is read before the next transform writes it
+            // E is read before the next transform writes it: the second row's reads are
+            // separated from the next item's transform by the barrier at the top of the loop
+            if (h == 0) __syncthreads();
         }
     }
     tmem_fence_before();
