@@ -832,8 +832,11 @@ __global__ void __launch_bounds__(L / 16, 3)
         tmem_store16(ta, reinterpret_cast<const cf*>(c0));
         if (t == 0) zr[(size_t)(L / 2) * nx * kTW] = mk(znyq, 0.f);
     }
-    __syncthreads();  // the first row's reads of the shared buffers are done
-    // row at position rp + 1: each tile's two cells with one store
+    // row at position rp + 1: each tile's two cells with one store.  No barrier between the
+    // rows: the first row last read the edge values before its transposition barrier and E
+    // before its unpack barrier, which every thread has passed, and this row writes U only
+    // after a barrier of its own (its solve's or its transform's), which no thread reaches
+    // before finishing the first row's unpack
     cf c0[16];
     const float znyq = rows_body<L, ORD>(
         smem_raw, t, ny, ord, nb, tw, sigma + (size_t)i1 * ny, [&](float(&x)[16]) { load(i1, x); }, [] {},
