@@ -287,7 +287,9 @@ tdg_status net_configure(tdg_batch_s* b) {
     }
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     std::vector<NetDisk> host(b->count);
-    std::vector<int> start(kPhases * (b->count + 1), 0);
+    // [3][count + 1] prefix sums of items per pass, then [3][count] the grids in each pass's
+    // order; both indexed by pass-local position
+    std::vector<int> start(kPhases * (b->count + 1) + kPhases * b->count, 0);
     for (int i = 0; i < b->count; ++i) {
         const int d = ord[i];
         const Plan& p = tdg_plan_internal(b->plans[d]);
@@ -318,9 +320,24 @@ tdg_status net_configure(tdg_batch_s* b) {
         g.nA = (g.uA + U - 1) / U;
         g.nB = (g.uB + U - 1) / U;
         g.nC = (g.uC + U - 1) / U;
-        start[0 * (b->count + 1) + i + 1] = start[0 * (b->count + 1) + i] + g.nA;
-        start[1 * (b->count + 1) + i + 1] = start[1 * (b->count + 1) + i] + g.nB;
-        start[2 * (b->count + 1) + i + 1] = start[2 * (b->count + 1) + i] + g.nC;
+    }
+    // each pass hands out its grids grouped by the length of the lines it transforms (rows:
+    // ly, columns: lx), longest first and by cost within a group, so that the blocks on an
+    // SM mostly run the same item body
+    for (int ph = 0; ph < kPhases; ++ph) {
+        std::vector<int> po(b->count);
+        for (int i = 0; i < b->count; ++i) po[i] = i;
+        std::stable_sort(po.begin(), po.end(), [&](int x, int y) {
+            const int lx = ph == 1 ? host[x].lx : host[x].ly, ly = ph == 1 ? host[y].lx : host[y].ly;
+            return lx > ly;
+        });
+        int* pref = start.data() + ph * (b->count + 1);
+        int* order = start.data() + kPhases * (b->count + 1) + ph * b->count;
+        for (int i = 0; i < b->count; ++i) {
+            const NetDisk& g = host[po[i]];
+            order[i] = po[i];
+            pref[i + 1] = pref[i] + (ph == 0 ? g.nA : (ph == 1 ? g.nB : g.nC));
+        }
     }
     int total = 0;
     for (int ph = 0; ph < kPhases; ++ph) total += start[ph * (b->count + 1) + b->count];
@@ -392,7 +409,7 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count, co
     if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->ndisks, count * sizeof(NetDisk));
-    if (e == cudaSuccess) e = cudaMalloc(&b->nstart, kPhases * (count + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->nstart, (kPhases * (count + 1) + kPhases * count) * sizeof(int));
     if (e != cudaSuccess) {
         batch_free(b);
         delete b;

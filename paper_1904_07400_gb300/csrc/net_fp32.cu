@@ -1915,7 +1915,7 @@ __global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev
     const int t = threadIdx.x;
     if (t < 32) tmem_alloc(&s_tmem, 64);
     // the items' prefix sums after the dynamic shared memory, when the batch is small enough
-    const int nstart = 3 * (b.count + 1);
+    const int nstart = 3 * (b.count + 1) + 3 * b.count;  // prefix sums, then the orders
     int* sstart = reinterpret_cast<int*>(smem_raw + kNetBatchSmem);
     const bool local = b.count <= kNetBatchMaxGrids;
     if (local)
@@ -1948,8 +1948,9 @@ __global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev
             local_item = item - totA - totB;
             pref = startC;
         }
-        const int d = find_grid(pref, b.count, local_item);
-        const int idx = local_item - pref[d];
+        const int pos = find_grid(pref, b.count, local_item);
+        const int idx = local_item - pref[pos];
+        const int d = st[3 * (b.count + 1) + phase * b.count + pos];
         const NetDisk& g = b.disks[d];
         if (t == 0) {
             int ok = 1;
@@ -2449,7 +2450,7 @@ int net_batch_units(const Plan& p, int pass) {
     return 2 * p.nx / per_y;
 }
 
-size_t net_batch_smem() { return kNetBatchSmem + 3 * (kNetBatchMaxGrids + 1) * sizeof(int); }
+size_t net_batch_smem() { return kNetBatchSmem + (3 * (kNetBatchMaxGrids + 1) + 3 * kNetBatchMaxGrids) * sizeof(int); }
 
 cudaError_t net_batch_blocks(int device, int* blocks) {
     cudaError_t e;

@@ -171,7 +171,7 @@ struct NetDisk {
 };
 struct NetBatchDev {
     const NetDisk* disks;
-    const int* start;      // [3][count + 1] prefix sums of items per pass
+    const int* start;      // [3][count + 1] prefix sums of items per pass, then [3][count] grid orders
     int* done;             // [3][count] finished items per pass and grid
     int* ticket;
     int* err;
