@@ -14,7 +14,7 @@ import torch
 
 # (threads, second knob): 64 is the persistent kernel on the network's item bodies with 1, 2,
 # 4 or 8 units per item; 256 and 512 the generic one with radix 8 (0) or radix 4 (1) first
-CANDIDATES = [(64, 1), (64, 2), (64, 4), (64, 8), (512, 0), (512, 1), (256, 0), (256, 1)]
+CANDIDATES = [(64, 1), (64, 2), (64, 4), (64, 8), (64, 16), (512, 0), (512, 1), (256, 0), (256, 1)]
 STREAMS = (2, 4, 8, 16)
 
 

@@ -464,7 +464,7 @@ tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref) {
     if (!b || (threads != 64 && threads != 256 && threads != 512)) return TDG_ERR_INVALID_ARG;
     if (threads == 64) {  // the persistent kernel on the network's item bodies; radix_pref: units per item
         const int u = radix_pref;
-        if (u != 1 && u != 2 && u != 4 && u != 8) return TDG_ERR_INVALID_ARG;
+        if (u != 1 && u != 2 && u != 4 && u != 8 && u != 16 && u != 32) return TDG_ERR_INVALID_ARG;
         if (!b->net_ok) return TDG_ERR_UNSUPPORTED;
         int prev = -1;
         cudaGetDevice(&prev);

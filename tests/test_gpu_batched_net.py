@@ -39,7 +39,7 @@ def _net_batch(plans, sig, units=2):
     return b
 
 
-@pytest.mark.parametrize("units", [1, 2, 4, 8])
+@pytest.mark.parametrize("units", [1, 2, 4, 8, 16, 32])
 def test_network_batch_equals_single_solves(grids, units):
     import torch
     plans, sig, ref = grids
