@@ -127,3 +127,26 @@ def test_network_form_refuses_grids_off_the_network_path(grids):
         with pytest.raises(native.TdgError):
             b = Batch([plans[0], extra], [sig[0], s])
             b.set_config(64, 2)
+
+
+def test_network_batch_beyond_the_shared_tables():
+    # more grids than the kernel keeps in shared memory: the item prefix sums and the
+    # per-pass grid orders are read from global memory; every grid still equals its own solve
+    import torch
+    from paper_1904_07400_gb300.api import Batch, Plan
+    library()
+    specs = [(128 + 16 * (d % 5), 128 + 16 * (d % 7), 1 + d % 3) for d in range(272)]
+    plans, sig, ref = [], [], []
+    for d, (nx, ny, k) in enumerate(specs):
+        p = Plan(nx, ny, k, 1.0 / nx, 1.0 / ny, precision="fp32")
+        s = torch.as_tensor(syn.clumps(nx, ny, seed=7000 + d), dtype=torch.float32, device=p.device)
+        plans.append(p)
+        sig.append(s)
+        ref.append(p.forces(s))
+    b = Batch(plans, sig)
+    b.set_config(64, 4)
+    b.launch()
+    torch.cuda.synchronize()
+    assert b.error() == 0
+    for (ax, ay), (bx, by) in zip(b.outs, ref):
+        assert torch.equal(ax, bx) and torch.equal(ay, by)
