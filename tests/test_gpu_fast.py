@@ -42,6 +42,20 @@ def test_fast_path_vs_fp64_gpu(shape, k):
     assert rel_l2_pair(*f32, *f64) <= TOL_FP32
 
 
+@pytest.mark.parametrize("shape", [(528, 2064), (1040, 1040), (272, 4080)])
+@pytest.mark.parametrize("k", [2, 3, 5])
+def test_row_pairs_with_rows_off_the_128_byte_pieces(shape, k):
+    # rows of 2048 and 4096 transform points run in pairs; rows whose length is not a
+    # multiple of 32 cells are loaded without the row TMA (their last 16 cells would not
+    # fill a 128-byte piece), the others by it
+    nx, ny = shape
+    dx, dy = 1.0 / nx, 1.0 / ny
+    sigma = syn.clumps(nx, ny, seed=nx + 3 * ny + k)
+    f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
+    f64 = _forces(nx, ny, k, dx, dy, "fp64", sigma)
+    assert rel_l2_pair(*f32, *f64) <= TOL_FP32
+
+
 @pytest.mark.parametrize("k", [1, 3])
 def test_fast_path_vs_oracle_nonsquare_cells(k):
     nx, ny = 1024, 2048
