@@ -1,5 +1,8 @@
-// Register FFT network of length L = 16 * R * 16 (R in {2, 4, 8, 16}) run by T = L / 16
-// threads with 16 complex values each, with ONE block barrier per transform.
+// Register FFT network of length L = 16 * R * 16 (R in {1, 2, 4, 8, 16}) run by T = L / 16
+// threads with 16 complex values each, with ONE block barrier per transform.  For R = 1
+// (L = 256, one half-warp) the first exchange and the middle stage are the identity: the
+// barrier stays (callers rely on it to order their own uses of the buffer), the data stay
+// in registers.
 //
 // Index decomposition: n = a + 16 b + 16 R c and k = k_c + 16 k_b + 16 R k_a
 // (a, k_a < 16; b, k_b < R; c, k_c < 16).  Three stages of butterflies:
@@ -41,7 +44,7 @@ struct Cfg {
     static constexpr int NM = 16 / R;  // stage-2 groups per thread
     static constexpr int SLAB = 272;
     static constexpr int BUF = R * SLAB;  // complex values per exchange buffer
-    static_assert(R == 2 || R == 4 || R == 8 || R == 16, "L in {512, 1024, 2048, 4096}");
+    static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "L in {256, 512, 1024, 2048, 4096}");
 };
 
 template <int L>
@@ -78,7 +81,9 @@ __device__ __forceinline__ cf csq(cf a) { return mk(a.x * a.x - a.y * a.y, 2.0f 
 template <int L>
 __device__ __forceinline__ void tw2(cf* v, cf b2) {
     constexpr int R = Cfg<L>::R;
-    if constexpr (R == 16) {
+    if constexpr (R == 1) {
+        // W_16^(0 k_c) = 1
+    } else if constexpr (R == 16) {
         const cf w4 = csq(csq(b2));
         reg::apply_powers<16>(v, b2, w4, csq(w4));
     } else if constexpr (R == 8) {
@@ -138,15 +143,19 @@ template <int L, typename TW, typename DF = CoreDft>
 __device__ __forceinline__ void fwd_p(cf* v, cf* buf, const TW& tw, int t, DF&& df = DF{}) {
     constexpr int R = Cfg<L>::R, NM = Cfg<L>::NM;
     df.template stage<16>(v);
-#pragma unroll
-    for (int kc = 0; kc < 16; ++kc) buf[(kc % R) * 272 + (kc / R) * 16 * R + t] = v[kc];
-    __syncthreads();
     const int a = t & 15;
     cf* slab = buf + (t >> 4) * 272;
+    if constexpr (R > 1) {
 #pragma unroll
-    for (int m = 0; m < NM; ++m)
+        for (int kc = 0; kc < 16; ++kc) buf[(kc % R) * 272 + (kc / R) * 16 * R + t] = v[kc];
+        __syncthreads();
 #pragma unroll
-        for (int b = 0; b < R; ++b) v[m * R + b] = slab[m * 16 * R + b * 16 + a];
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int b = 0; b < R; ++b) v[m * R + b] = slab[m * 16 * R + b * 16 + a];
+    } else {
+        __syncthreads();
+    }
     tw.apply2(v);
     df.template stage<R>(v);
     __syncwarp();
@@ -181,14 +190,18 @@ __device__ __forceinline__ void inv_t_p(cf* v, cf* buf, const TW& tw, int t, DF&
     for (int s = 0; s < 16; ++s) v[s] = slab[s * 17 + a];
     df.template stage<R>(v);
     tw.apply2(v);
-    __syncwarp();
+    if constexpr (R > 1) {
+        __syncwarp();
 #pragma unroll
-    for (int m = 0; m < NM; ++m)
+        for (int m = 0; m < NM; ++m)
 #pragma unroll
-        for (int b = 0; b < R; ++b) slab[m * 16 * R + b * 16 + a] = v[m * R + b];
-    __syncthreads();
+            for (int b = 0; b < R; ++b) slab[m * 16 * R + b * 16 + a] = v[m * R + b];
+        __syncthreads();
 #pragma unroll
-    for (int kc = 0; kc < 16; ++kc) v[kc] = buf[(kc % R) * 272 + (kc / R) * 16 * R + t];
+        for (int kc = 0; kc < 16; ++kc) v[kc] = buf[(kc % R) * 272 + (kc / R) * 16 * R + t];
+    } else {
+        __syncthreads();
+    }
     df.template stage<16>(v);
 }
 

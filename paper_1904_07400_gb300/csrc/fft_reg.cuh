@@ -1,5 +1,5 @@
 // Register butterflies and twiddle helpers of the transform network (fft_net.cuh): radix
-// 2, 4, 8 and 16 DFTs on a thread's 16 complex values, powers of a twiddle base, the
+// 1, 2, 4, 8 and 16 DFTs on a thread's 16 complex values, powers of a twiddle base, the
 // per-element twist W_2L^(t + r T) of the padded column transform, and the padded
 // shared-memory index.
 #pragma once
@@ -103,7 +103,9 @@ __device__ __forceinline__ void dft16(cf* a) {
 // v[b * R .. b * R + R - 1] (element r at v[b * R + r])
 template <int R>
 __device__ __forceinline__ void butterflies(cf* v) {
-    if constexpr (R == 16) {
+    if constexpr (R == 1) {
+        // radix 1: nothing to do (the 16 * 1 * 16 network has no middle stage)
+    } else if constexpr (R == 16) {
         dft16(v);
     } else if constexpr (R == 8) {
         dft8<1>(v);

@@ -1,6 +1,7 @@
 // FP32 force solve (and its adjoint) for grids whose sides are multiples of 16 from 128 to
-// 4096 cells, padded to transform lengths L in {512, 1024, 2048, 4096}, built around the
-// one-barrier register FFT network of fft_net.cuh and the data movement of sm_103a:
+// 4096 cells, padded to transform lengths L in {256, 512, 1024, 2048, 4096}, built around
+// the one-barrier register FFT network of fft_net.cuh and the data movement of sm_103a
+// (lines of 256 points are half a warp: their kernels run two lines per 32-thread block):
 //
 //  * pass A (rows): chunked register spline solve, packed real transform, unpack, and
 //    16-byte stores of the row's cells into the tiled intermediate Z;
@@ -364,6 +365,13 @@ __device__ __forceinline__ void flag_error(int* err, int code) {
 }
 
 constexpr int kBox = 256;  // tile cells per TMA box (the box-dimension limit)
+
+// shared values of the chunked spline solve's edge exchange (solve_chunk_*): four per warp
+// of the line's threads, and four for a line of half a warp (T = 16)
+template <int T>
+__host__ __device__ constexpr int edge_slots() {
+    return 4 * (T / 32 > 0 ? T / 32 : 1);
+}
 
 // ---------------------------------------------------------------------------------------
 // Tensor memory (tcgen05) as a per-thread stash of 16 complex values: warp w uses TMEM
@@ -754,7 +762,7 @@ __device__ __forceinline__ void st_global_v8(void* p, float4 a, float4 b) {
 // and the tensor-memory address.
 template <int L>
 constexpr size_t rows2_bytes() {
-    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(float) + 16;
+    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + edge_slots<L / 16>() * sizeof(float) + 16;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -775,7 +783,7 @@ __global__ void __launch_bounds__(L / 16, 3)
     constexpr int BUF = net::Cfg<L>::BUF;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned long long* bar =
-        reinterpret_cast<unsigned long long*>(smem_raw + 2 * BUF * sizeof(cf) + 4 * (T / 32) * sizeof(float));
+        reinterpret_cast<unsigned long long*>(smem_raw + 2 * BUF * sizeof(cf) + edge_slots<T>() * sizeof(float));
     unsigned* tslot = reinterpret_cast<unsigned*>(bar + 1);
     const int t = threadIdx.x;
     const bool solve = ORD < 0 ? ord != 0 : ORD != 0;
@@ -859,7 +867,8 @@ __global__ void __launch_bounds__(L / 16, 3)
 // ---------------------------------------------------------------------------------------
 template <int L>
 constexpr int inv_e_offset() {
-    return (((L + 2) * 8 + 1023) / 1024) * 1024;  // bytes
+    constexpr int a = L >= 512 ? 1024 : 128;  // 256-length rows: four of them share a batch block
+    return (((L + 2) * 8 + a - 1) / a) * a;   // bytes
 }
 
 
@@ -1203,7 +1212,7 @@ constexpr bool cols_twiddles_in_tmem() {
 template <int L>
 constexpr size_t cols_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF) * sizeof(cf) + 4 * (T / 32) * sizeof(cf) + 16 +
+    return (size_t)(2 * BUF) * sizeof(cf) + edge_slots<T>() * sizeof(cf) + 16 +
            (Stash<L>::kTmem ? 0 : (size_t)2 * 16 * T * sizeof(cf));
 }
 
@@ -1234,7 +1243,7 @@ __device__ __forceinline__ void cols_item(unsigned char* smem, int t, int kl, in
     cf* E = reinterpret_cast<cf*>(smem);  // network buffer
     cf* xb = E + BUF;                     // the column (padded natural), later the even x result
     cf* edge = xb + BUF;
-    cf* sslots = reinterpret_cast<cf*>(reinterpret_cast<unsigned*>(edge + 4 * (T / 32)) + 4);  // shared stash slots A, B
+    cf* sslots = reinterpret_cast<cf*>(reinterpret_cast<unsigned*>(edge + edge_slots<T>()) + 4);  // shared stash slots A, B
     const int tile = kl >> 1, c = kl & 1;
     const size_t slab = (size_t)nx * kTW;
     const cf* zc = z + (size_t)tile * slab + c;
@@ -1362,7 +1371,7 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
     constexpr unsigned kCols = cols_twiddles_in_tmem<L>() ? 256 : (T > 128 ? 128 : 64);
     constexpr int BUF = net::Cfg<L>::BUF;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned* tslot = reinterpret_cast<unsigned*>(reinterpret_cast<cf*>(smem_raw) + 2 * BUF + 4 * (T / 32));
+    unsigned* tslot = reinterpret_cast<unsigned*>(reinterpret_cast<cf*>(smem_raw) + 2 * BUF + edge_slots<T>());
     const int t = threadIdx.x;
     if constexpr (kTm) {
         if (t < 32) tmem_alloc(tslot, kCols);
@@ -1386,7 +1395,7 @@ __global__ void __launch_bounds__(L / 16, cols_min_blocks<L>())
 template <int L>
 constexpr size_t tc_cols_bmat_offset() {  // bytes: E, xb, edge, tensor slot and mbarriers, aligned
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (((size_t)(2 * BUF) * sizeof(cf) + 4 * (T / 32) * sizeof(cf) + 32 + 1023) / 1024) * 1024;
+    return (((size_t)(2 * BUF) * sizeof(cf) + edge_slots<T>() * sizeof(cf) + 32 + 1023) / 1024) * 1024;
 }
 template <int L>
 constexpr size_t tc_cols_smem_bytes() {
@@ -1407,7 +1416,7 @@ __global__ void __launch_bounds__(L / 16, 2)
     cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
     cf* xb = E + BUF;                         // the column (padded natural), later the even x result
     cf* edge = xb + BUF;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 4 * (T / 32));
+    unsigned* tslot = reinterpret_cast<unsigned*>(edge + edge_slots<T>());
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(tslot + 4);  // one per warp group
     float* bsm = reinterpret_cast<float*>(smem_raw + tc_cols_bmat_offset<L>());
     cf* sslot = reinterpret_cast<cf*>(bsm + kTcBFloats);  // stash slot A, [r][t]
@@ -1567,29 +1576,25 @@ __device__ __forceinline__ void adj_products(cf* v, const float2* __restrict__ s
 // pass B of the adjoint: column ky of Z_x and Z_y (natural rows) -> G column, x solve
 // applied, rows stored at the chunk-permuted positions (i % 16) (nx / 16) + i / 16.
 // Stashes: A, B in tensor memory (shared slots for 512), C in xb (shared, own slots).
+// The body of one column (thread t of the column's T threads, shared memory `smem`, column
+// ky); `store` false: the column is computed but nothing is stored (a half-warp that has no
+// column of its own in a block of two columns).  TMEM address at *tslot (L >= 1024).
 template <int L>
-__global__ void __launch_bounds__(L / 16, 2)
-    k_net_cols_adj(const cf* __restrict__ zx, const cf* __restrict__ zy, int nx, int solve,
-                   const cf* __restrict__ nb, const cf* __restrict__ tw, const float2* __restrict__ spec,
-                   cf* __restrict__ g) {
+__device__ __forceinline__ void cols_adj_item(unsigned char* smem, int t, int ky, bool store,
+                                              const cf* __restrict__ zx, const cf* __restrict__ zy, int nx, int solve,
+                                              const cf* __restrict__ nb, const cf* __restrict__ tw,
+                                              const float2* __restrict__ spec, cf* __restrict__ g,
+                                              const unsigned* tslot) {
     constexpr int T = L / 16;
     constexpr int BUF = net::Cfg<L>::BUF;
     constexpr int HS = L / 2 + 2;
     constexpr bool kTm = Stash<L>::kTmem;
     constexpr bool kTwt = cols_twiddles_in_tmem<L>();
     constexpr unsigned kWarpCols = kTwt ? 128 : 64;
-    constexpr unsigned kCols = kTwt ? 256 : (T > 128 ? 128 : 64);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    cf* E = reinterpret_cast<cf*>(smem_raw);  // network buffer
-    cf* xb = E + BUF;                         // stash C ([r][t]), then the solve's transposition
+    cf* E = reinterpret_cast<cf*>(smem);  // network buffer
+    cf* xb = E + BUF;                     // stash C ([r][t]), then the solve's transposition
     cf* edge = xb + BUF;
-    unsigned* tslot = reinterpret_cast<unsigned*>(edge + 4 * (T / 32));
-    cf* sslots = reinterpret_cast<cf*>(tslot + 4);
-    const int t = threadIdx.x;
-    if constexpr (kTm) {
-        if (t < 32) tmem_alloc(tslot, kCols);
-    }
-    const int ky = blockIdx.x;
+    cf* sslots = reinterpret_cast<cf*>(reinterpret_cast<unsigned*>(edge + edge_slots<T>()) + 4);
     const int tile = ky >> 1, c = ky & 1;
     const size_t slab = (size_t)nx * kTW;
     const float2* se = spec + (size_t)ky * 2 * HS;
@@ -1694,17 +1699,35 @@ __global__ void __launch_bounds__(L / 16, 2)
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = xb[pad(16 * t + r)];
         solve_chunk<cf>(v, t, nact, T, edge, solve);
-        if (t < nact) {
+        if (store && t < nact) {
 #pragma unroll
             for (int r = 0; r < 16; ++r) gc[(size_t)(r * nact + t) * kTW] = v[r];
         }
-    } else {
+    } else if (store) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int n = t + r * T;
             if (n < nx) gc[(size_t)((n & 15) * nact + (n >> 4)) * kTW] = v[r];
         }
     }
+}
+
+template <int L>
+__global__ void __launch_bounds__(L / 16, 2)
+    k_net_cols_adj(const cf* __restrict__ zx, const cf* __restrict__ zy, int nx, int solve,
+                   const cf* __restrict__ nb, const cf* __restrict__ tw, const float2* __restrict__ spec,
+                   cf* __restrict__ g) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    constexpr bool kTm = Stash<L>::kTmem;
+    constexpr unsigned kCols = cols_twiddles_in_tmem<L>() ? 256 : (T > 128 ? 128 : 64);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned* tslot = reinterpret_cast<unsigned*>(reinterpret_cast<cf*>(smem_raw) + 2 * BUF + edge_slots<T>());
+    const int t = threadIdx.x;
+    if constexpr (kTm) {
+        if (t < 32) tmem_alloc(tslot, kCols);
+    }
+    cols_adj_item<L>(smem_raw, t, blockIdx.x, true, zx, zy, nx, solve, nb, tw, spec, g, tslot);
     if constexpr (kTm) {
         tmem_fence_before();
         __syncthreads();
@@ -1716,7 +1739,7 @@ __global__ void __launch_bounds__(L / 16, 2)
 template <int L>
 constexpr size_t cols_adj_smem_bytes() {
     constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
-    return (size_t)(2 * BUF) * sizeof(cf) + 4 * (T / 32) * sizeof(cf) + 16 +
+    return (size_t)(2 * BUF) * sizeof(cf) + edge_slots<T>() * sizeof(cf) + 16 +
            (Stash<L>::kTmem ? 0 : (size_t)2 * 16 * T * sizeof(cf));
 }
 
@@ -1802,7 +1825,7 @@ __global__ void __launch_bounds__(L / 16, 3)
 
 template <int L>
 size_t inv_adj_bytes() {
-    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16 + 4 * (L / 16 / 32) * sizeof(float);
+    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + 16 + edge_slots<L / 16>() * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1819,13 +1842,13 @@ constexpr long long kNetSpinLimit = 1000000;  // ~1 s with 1 us naps
 
 template <int L>
 constexpr size_t batch_item_bytes() {  // shared memory of one transform's item, any pass
-    constexpr size_t a = (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(float);
-    constexpr size_t b = (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(cf) + 16;
+    constexpr size_t a = (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + edge_slots<L / 16>() * sizeof(float);
+    constexpr size_t b = (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + edge_slots<L / 16>() * sizeof(cf) + 16;
     constexpr size_t c = (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf);
     return ((std::max(a, std::max(b, c)) + 1023) / 1024) * 1024;
 }
-constexpr size_t kNetBatchSmem =
-    batch_item_bytes<1024>() > 2 * batch_item_bytes<512>() ? batch_item_bytes<1024>() : 2 * batch_item_bytes<512>();
+constexpr size_t kNetBatchSmem = std::max(batch_item_bytes<1024>(),
+                                          std::max(2 * batch_item_bytes<512>(), 4 * batch_item_bytes<256>()));
 
 __device__ __forceinline__ int find_grid(const int* pref, int count, int item) {
     int lo = 0, hi = count;  // pref[lo] <= item < pref[hi]
@@ -1908,6 +1931,45 @@ __device__ __noinline__ void bitem_inv512(unsigned char* sm, const NetDisk& g, i
     }
 }
 
+// 256-length lines: one per half-warp, four per unit
+__device__ __noinline__ void bitem_rows256(unsigned char* sm, const NetDisk& g, int u0, int u1) {
+    const int q = threadIdx.x >> 4;
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) __syncthreads();
+        rows_item<256, -1>(sm + q * batch_item_bytes<256>(), threadIdx.x & 15, 4 * u + q, g.sigma, g.ny, g.ord,
+                           g.ord != 0, g.nx, reinterpret_cast<const cf*>(g.nby), reinterpret_cast<const cf*>(g.twy),
+                           reinterpret_cast<cf*>(g.z));
+    }
+}
+__device__ __noinline__ void bitem_cols256(unsigned char* sm, const NetDisk& g, int u0, int u1, const unsigned* tm) {
+    const int q = threadIdx.x >> 4;
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) {
+            tmem_fence_before();
+            __syncthreads();
+            tmem_fence_after();
+        }
+        const int col = 4 * u + q;  // past the last column: computed again, not stored
+        const bool real = col < g.hy;
+        const int c = real ? col : g.hy - 1;
+        cols_item<256, -1, true>(sm + q * batch_item_bytes<256>(), threadIdx.x & 15, c, c,
+                                 reinterpret_cast<const cf*>(g.z), g.nx, real ? g.nx : 0, g.ord,
+                                 reinterpret_cast<const cf*>(g.nbx), reinterpret_cast<const cf*>(g.twx),
+                                 reinterpret_cast<const float2*>(g.spec), reinterpret_cast<cf*>(g.gx),
+                                 reinterpret_cast<cf*>(g.gy), tm);
+    }
+}
+__device__ __noinline__ void bitem_inv256(unsigned char* sm, const NetDisk& g, int u0, int u1) {
+    const int q = threadIdx.x >> 4;
+    for (int u = u0; u < u1; ++u) {
+        if (u > u0) __syncthreads();
+        const int rc = 4 * u + q, comp = rc / g.nx, i = rc - comp * g.nx;
+        inv_item<256>(sm + q * batch_item_bytes<256>(), threadIdx.x & 15, i,
+                      reinterpret_cast<const cf*>(comp ? g.gy : g.gx), g.nx, g.ny, reinterpret_cast<const cf*>(g.nby),
+                      reinterpret_cast<const cf*>(g.twy), comp ? g.fy : g.fx);
+    }
+}
+
 __global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev b) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int s_item, s_ok;
@@ -1979,13 +2041,16 @@ __global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev
             const int u0 = idx * b.units, u1 = min(u0 + b.units, units);
             if (phase == 0) {
                 if (g.ly == 1024) bitem_rows1024(smem_raw, g, u0, u1);
-                else bitem_rows512(smem_raw, g, u0, u1);
+                else if (g.ly == 512) bitem_rows512(smem_raw, g, u0, u1);
+                else bitem_rows256(smem_raw, g, u0, u1);
             } else if (phase == 1) {
                 if (g.lx == 1024) bitem_cols1024(smem_raw, g, u0, u1, &s_tmem);
-                else bitem_cols512(smem_raw, g, u0, u1, &s_tmem);
+                else if (g.lx == 512) bitem_cols512(smem_raw, g, u0, u1, &s_tmem);
+                else bitem_cols256(smem_raw, g, u0, u1, &s_tmem);
             } else {
                 if (g.ly == 1024) bitem_inv1024(smem_raw, g, u0, u1);
-                else bitem_inv512(smem_raw, g, u0, u1);
+                else if (g.ly == 512) bitem_inv512(smem_raw, g, u0, u1);
+                else bitem_inv256(smem_raw, g, u0, u1);
             }
         }
         tmem_fence_before();
@@ -2000,6 +2065,163 @@ __global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev
     __syncthreads();
     tmem_fence_after();
     if (t < 32) tmem_dealloc(s_tmem, 64);
+}
+
+// ---------------------------------------------------------------------------------------
+// L = 256: a line is half a warp (T = 16), so these kernels run two lines per 32-thread
+// block, each half-warp on its own shared-memory region (the item bodies above, thread
+// t = threadIdx.x % 16).  Both halves pass the same block barriers; a half with no line of
+// its own (an odd count of columns) computes the last column again and stores nothing.
+// ---------------------------------------------------------------------------------------
+template <size_t B>
+constexpr size_t item_stride() {
+    return ((B + 127) / 128) * 128;
+}
+
+// pass C of the adjoint for one row i of G (stored at its chunk-permuted position) with
+// plain 16-byte loads: the body of k_net_rows_inv_adj for the half-warp lines
+template <int L>
+constexpr size_t inv_adj_item_bytes() {
+    return (size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf) + edge_slots<L / 16>() * sizeof(float);
+}
+
+template <int L>
+__device__ __forceinline__ void inv_adj_item(unsigned char* smem, int t, int i, const cf* __restrict__ g, int nx,
+                                             int ny, int solve, const cf* __restrict__ nb,
+                                             const cf* __restrict__ tw, float* __restrict__ out) {
+    constexpr int T = L / 16;
+    constexpr int BUF = net::Cfg<L>::BUF;
+    cf* S = reinterpret_cast<cf*>(smem);
+    cf* E = reinterpret_cast<cf*>(smem + inv_e_offset<L>());
+    float* edge = reinterpret_cast<float*>(E + BUF);
+    const int nq = nx >> 4;
+    const cf* gr = g + (size_t)((i & 15) * nq + (i >> 4)) * kTW;
+#pragma unroll
+    for (int q = 0; q < L / 2 / T; ++q) {
+        const int p = t + T * q;
+        *reinterpret_cast<float4*>(S + 2 * p) = __ldg(reinterpret_cast<const float4*>(gr + (size_t)p * nx * kTW));
+    }
+    if (t == 0) S[L] = ld2(gr + (size_t)(L / 2) * nx * kTW);
+    __syncthreads();
+    const net::Bases bs = net::load_bases<L>(nb, t);
+    const cf wt = reg::ld_tw(tw, t);
+    const int pt = net::perm<L>(t);
+    cf v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = t + T * r;
+        v[r] = conjg(pack_c2r(S[k], S[L - k], reg::twist(wt, r)));
+    }
+    net::fwd<L>(v, E, bs, t);
+    __syncthreads();  // every half-warp is done with its slab of E
+#pragma unroll
+    for (int ka = 0; ka < 8; ++ka) E[pad(pt + T * ka)] = conjg(v[ka]);
+    __syncthreads();
+    float* row = out + (size_t)i * ny;
+    if (solve) {
+        // pairs 8 t .. 8 t + 7 = reals 16 t .. 16 t + 15 of the row
+        const int nact = ny >> 4;
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const cf o = E[pad(8 * t + j)];
+            x[2 * j] = o.x;
+            x[2 * j + 1] = o.y;
+        }
+        solve_chunk<float>(x, t, nact, T, edge, solve);
+        if (t < nact) {
+            float4* dst = reinterpret_cast<float4*>(row) + 4 * t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        }
+    } else {
+        float2* dst = reinterpret_cast<float2*>(row);
+#pragma unroll
+        for (int c2 = 0; c2 < 8; ++c2) {
+            const int n = t + T * c2;
+            const cf o = E[pad(n)];
+            if (2 * n < ny) dst[n] = make_float2(o.x, o.y);
+        }
+    }
+}
+
+template <int L>
+constexpr size_t rows_h_stride() {
+    return item_stride<(size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + edge_slots<L / 16>() * sizeof(float)>();
+}
+template <int L>
+constexpr size_t cols_h_stride() {
+    constexpr int T = L / 16, BUF = net::Cfg<L>::BUF;
+    return item_stride<(size_t)(2 * BUF) * sizeof(cf) + edge_slots<T>() * sizeof(cf) + 16 +
+                       (size_t)2 * 16 * T * sizeof(cf)>();
+}
+template <int L>
+constexpr size_t inv_h_stride() {
+    return item_stride<(size_t)inv_e_offset<L>() + net::Cfg<L>::BUF * sizeof(cf)>();
+}
+template <int L>
+constexpr size_t inv_adj_h_stride() {
+    return item_stride<inv_adj_item_bytes<L>()>();
+}
+
+template <int L, int ORD>
+__global__ void __launch_bounds__(32) k_net_rows_h(const float* __restrict__ sigma, int ny, int ord, int rowmap,
+                                                   int nx, const cf* __restrict__ nb, const cf* __restrict__ tw,
+                                                   cf* __restrict__ z) {
+    static_assert(L / 16 == 16, "half-warp lines");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int h = threadIdx.x >> 4;
+    rows_item<L, ORD>(smem_raw + h * rows_h_stride<L>(), threadIdx.x & 15, 2 * blockIdx.x + h, sigma, ny, ord,
+                      rowmap, nx, nb, tw, z);
+}
+
+// columns ky0 .. ky0 + nky - 1 (Z, G_x, G_y hold them from ky0 on)
+template <int L, int ORD>
+__global__ void __launch_bounds__(32) k_net_cols_h(const cf* __restrict__ z, int nx, int ord, const cf* __restrict__ nb,
+                                                   const cf* __restrict__ tw, const float2* __restrict__ spec,
+                                                   cf* __restrict__ gx, cf* __restrict__ gy, int ky0, int nky) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int h = threadIdx.x >> 4;
+    const int kl = 2 * blockIdx.x + h;
+    const bool act = kl < nky;
+    const int k = act ? kl : nky - 1;
+    cols_item<L, ORD, false>(smem_raw + h * cols_h_stride<L>(), threadIdx.x & 15, k, ky0 + k, z, nx, act ? nx : 0, ord,
+                             nb, tw, spec, gx, gy, nullptr);
+}
+
+template <int L>
+__global__ void __launch_bounds__(32) k_net_rows_inv_h(const cf* __restrict__ g0, const cf* __restrict__ g1, int nx,
+                                                       int ny, const cf* __restrict__ nb, const cf* __restrict__ tw,
+                                                       float* __restrict__ f0, float* __restrict__ f1) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int h = threadIdx.x >> 4;
+    const int w = 2 * blockIdx.x + h;
+    const int comp = w / nx, i = w - comp * nx;
+    inv_item<L>(smem_raw + h * inv_h_stride<L>(), threadIdx.x & 15, i, comp ? g1 : g0, nx, ny, nb, tw,
+                comp ? f1 : f0);
+}
+
+template <int L>
+__global__ void __launch_bounds__(32) k_net_cols_adj_h(const cf* __restrict__ zx, const cf* __restrict__ zy, int nx,
+                                                       int solve, int hy, const cf* __restrict__ nb,
+                                                       const cf* __restrict__ tw, const float2* __restrict__ spec,
+                                                       cf* __restrict__ g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int h = threadIdx.x >> 4;
+    const int ky = 2 * blockIdx.x + h;
+    const bool act = ky < hy;
+    cols_adj_item<L>(smem_raw + h * cols_h_stride<L>(), threadIdx.x & 15, act ? ky : hy - 1, act, zx, zy, nx, solve,
+                     nb, tw, spec, g, nullptr);
+}
+
+template <int L>
+__global__ void __launch_bounds__(32) k_net_rows_inv_adj_h(const cf* __restrict__ g, int nx, int ny, int solve,
+                                                           const cf* __restrict__ nb, const cf* __restrict__ tw,
+                                                           float* __restrict__ out) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int h = threadIdx.x >> 4;
+    inv_adj_item<L>(smem_raw + h * inv_adj_h_stride<L>(), threadIdx.x & 15, 2 * blockIdx.x + h, g, nx, ny, solve, nb,
+                    tw, out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2051,7 +2273,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <int L>
 size_t rows_bytes() {
-    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + 4 * (L / 16 / 32) * sizeof(float);
+    return (size_t)2 * net::Cfg<L>::BUF * sizeof(cf) + edge_slots<L / 16>() * sizeof(float);
 }
 
 template <int L>
@@ -2084,6 +2306,12 @@ cudaError_t launch_rows(const float* sigma, int ny, int ord, int nx, const cf* n
                         cudaStream_t s) {
     size_t sm = rows_bytes<LY>();
     cudaError_t e;
+    if constexpr (LY == 256) {  // two rows per 32-thread block
+        sm = 2 * rows_h_stride<LY>();
+        if ((e = set_smem(k_net_rows_h<LY, OR>, sm))) return e;
+        k_net_rows_h<LY, OR><<<nx / 2, 32, sm, s>>>(sigma, ny, ord, ord != 0, nx, nb, tw, z);
+        return cudaGetLastError();
+    }
     if constexpr (LY >= 2048) {
         // solved rows of whole 128-byte pieces by TMA: a map of sigma as {32 floats, ny / 32
         // pieces, nx rows}, one row per box, 128-byte swizzle
@@ -2144,6 +2372,12 @@ cudaError_t launch_rows_inv(const cf* g0, const cf* g1, int nx, int ntile, int n
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
     const size_t comp_bytes = (size_t)(g1 - g0) * sizeof(cf);
+    if constexpr (LY == 256) {  // two rows per 32-thread block, plain loads
+        const size_t sm = 2 * inv_h_stride<LY>();
+        if ((e = set_smem(k_net_rows_inv_h<LY>, sm))) return e;
+        k_net_rows_inv_h<LY><<<nx, 32, sm, s>>>(g0, g1, nx, ny, nb, tw, fx, fy);
+        return cudaGetLastError();
+    }
     CUtensorMap gmap;
     if constexpr (LY >= 2048) {
         // pair view: cells of 4 complex (rows 2j and 2j + 1 of one tile), nx / 2 pairs
@@ -2164,6 +2398,24 @@ cudaError_t launch_rows_inv(const cf* g0, const cf* g1, int nx, int ntile, int n
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_rows_inv<LY>, LY / 16, sm))) return e;
         const int grid = std::min(2 * nx, std::max(1, per_sm) * nsm);
         k_net_rows_inv<LY><<<grid, LY / 16, sm, s>>>(gmap, g0, g1, nx, ny, nb, tw, fx, fy, err);
+    }
+    return cudaGetLastError();
+}
+
+// Pass B over columns ky0 .. ky0 + nky - 1 (FP32 form): one column per block, two per
+// 32-thread block for L = 256
+template <int LX, int OC>
+cudaError_t launch_cols(const cf* z, int nx, int ord, const cf* nb, const cf* tw, const float2* spec, cf* gx, cf* gy,
+                        int ky0, int nky, cudaStream_t s) {
+    cudaError_t e;
+    if constexpr (LX == 256) {
+        const size_t sm = 2 * cols_h_stride<LX>();
+        if ((e = set_smem(k_net_cols_h<LX, OC>, sm))) return e;
+        k_net_cols_h<LX, OC><<<(nky + 1) / 2, 32, sm, s>>>(z, nx, ord, nb, tw, spec, gx, gy, ky0, nky);
+    } else {
+        const size_t sm = cols_smem_bytes<LX>();
+        if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
+        k_net_cols<LX, OC><<<nky, LX / 16, sm, s>>>(z, nx, ord, nb, tw, spec, gx, gy, ky0);
     }
     return cudaGetLastError();
 }
@@ -2201,10 +2453,9 @@ cudaError_t run_net_o(const Plan& p, const float* sigma, float* fx, float* fy, v
         }
     }
     if (p.prec != TDG_FP32_TC16) {
-        sm = cols_smem_bytes<LX>();
-        if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
-        k_net_cols<LX, OC><<<hy, LX / 16, sm, s>>>(z, p.nx, ord, bases_x(p), twx,
-                                               reinterpret_cast<const float2*>(p.spec_half), gx, gy, 0);
+        if ((e = launch_cols<LX, OC>(z, p.nx, ord, bases_x(p), twx, reinterpret_cast<const float2*>(p.spec_half), gx,
+                                     gy, 0, hy, s)))
+            return e;
     }
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
@@ -2231,13 +2482,8 @@ cudaError_t slab_rows_o(const Plan& p, const float* sigma_rows, int nrows, cf* z
 template <int LX, int ORD>
 cudaError_t slab_cols_o(const Plan& p, const cf* zc, int ky0, int nky, cf* gxc, cf* gyc, cudaStream_t s) {
     constexpr int OC = LX == 4096 ? ORD : -1;
-    const size_t sm = cols_smem_bytes<LX>();
-    cudaError_t e;
-    if ((e = set_smem(k_net_cols<LX, OC>, sm))) return e;
-    k_net_cols<LX, OC><<<nky, LX / 16, sm, s>>>(zc, p.nx, solve_order(p), bases_x(p),
-                                                reinterpret_cast<const cf*>(p.tw_x),
-                                                reinterpret_cast<const float2*>(p.spec_half), gxc, gyc, ky0);
-    return cudaGetLastError();
+    return launch_cols<LX, OC>(zc, p.nx, solve_order(p), bases_x(p), reinterpret_cast<const cf*>(p.tw_x),
+                               reinterpret_cast<const float2*>(p.spec_half), gxc, gyc, ky0, nky, s);
 }
 
 template <int LY>
@@ -2291,8 +2537,6 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     const cf* twy = reinterpret_cast<const cf*>(p.tw_y);
     const int solve = solve_order(p);
     cudaError_t e;
-    CUtensorMap gmap;
-    if ((e = encode_tiles(&gmap, g, p.nx, ntile, 1, 0, true))) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
@@ -2300,12 +2544,30 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
     if ((e = launch_rows<LY, 0>(gxin, p.ny, 0, p.nx, bases_y(p), twy, zx, p.err, s))) return e;
     if ((e = launch_rows<LY, 0>(gyin, p.ny, 0, p.nx, bases_y(p), twy, zy, p.err, s))) return e;
     mark(p, 1, s);
-    size_t sm = cols_adj_smem_bytes<LX>();
-    if ((e = set_smem(k_net_cols_adj<LX>, sm))) return e;
-    k_net_cols_adj<LX><<<hy, LX / 16, sm, s>>>(zx, zy, p.nx, solve, bases_x(p), twx,
-                                               reinterpret_cast<const float2*>(p.spec_half), g);
+    size_t sm;
+    if constexpr (LX == 256) {  // two columns per 32-thread block
+        sm = 2 * cols_h_stride<LX>();
+        if ((e = set_smem(k_net_cols_adj_h<LX>, sm))) return e;
+        k_net_cols_adj_h<LX><<<(hy + 1) / 2, 32, sm, s>>>(zx, zy, p.nx, solve, hy, bases_x(p), twx,
+                                                         reinterpret_cast<const float2*>(p.spec_half), g);
+    } else {
+        sm = cols_adj_smem_bytes<LX>();
+        if ((e = set_smem(k_net_cols_adj<LX>, sm))) return e;
+        k_net_cols_adj<LX><<<hy, LX / 16, sm, s>>>(zx, zy, p.nx, solve, bases_x(p), twx,
+                                                   reinterpret_cast<const float2*>(p.spec_half), g);
+    }
     if ((e = cudaGetLastError())) return e;
     mark(p, 2, s);
+    if constexpr (LY == 256) {  // two rows per 32-thread block, plain loads
+        sm = 2 * inv_adj_h_stride<LY>();
+        if ((e = set_smem(k_net_rows_inv_adj_h<LY>, sm))) return e;
+        k_net_rows_inv_adj_h<LY><<<p.nx / 2, 32, sm, s>>>(g, p.nx, p.ny, solve, bases_y(p), twy, gsig);
+        e = cudaGetLastError();
+        mark(p, 3, s);
+        return e;
+    }
+    CUtensorMap gmap;
+    if ((e = encode_tiles(&gmap, g, p.nx, ntile, 1, 0, true))) return e;
     sm = inv_adj_bytes<LY>();
     if ((e = set_smem(k_net_rows_inv_adj<LY>, sm))) return e;
     int per_sm = 0;
@@ -2321,6 +2583,7 @@ cudaError_t run_net_adj(const Plan& p, const float* gxin, const float* gyin, flo
 template <int LX>
 cudaError_t run_net_adj_x(const Plan& p, const float* gx, const float* gy, float* gs, void* work, cudaStream_t s) {
     switch (len_y(p)) {
+        case 256: return run_net_adj<LX, 256>(p, gx, gy, gs, work, s);
         case 512: return run_net_adj<LX, 512>(p, gx, gy, gs, work, s);
         case 1024: return run_net_adj<LX, 1024>(p, gx, gy, gs, work, s);
         case 2048: return run_net_adj<LX, 2048>(p, gx, gy, gs, work, s);
@@ -2331,6 +2594,7 @@ cudaError_t run_net_adj_x(const Plan& p, const float* gx, const float* gy, float
 template <int LX>
 cudaError_t run_net_x(const Plan& p, const float* sigma, float* fx, float* fy, void* work, cudaStream_t s) {
     switch (len_y(p)) {
+        case 256: return run_net<LX, 256>(p, sigma, fx, fy, work, s);
         case 512: return run_net<LX, 512>(p, sigma, fx, fy, work, s);
         case 1024: return run_net<LX, 1024>(p, sigma, fx, fy, work, s);
         case 2048: return run_net<LX, 2048>(p, sigma, fx, fy, work, s);
@@ -2346,6 +2610,7 @@ cudaError_t build_axis(cf* tab, cudaStream_t s) {
 
 cudaError_t build_bases(cf* tab, int n, cudaStream_t s) {
     switch (n) {
+        case 256: return build_axis<256>(tab, s);
         case 512: return build_axis<512>(tab, s);
         case 1024: return build_axis<1024>(tab, s);
         case 2048: return build_axis<2048>(tab, s);
@@ -2365,7 +2630,7 @@ cudaError_t spectra_axis(const Plan& p, cudaStream_t s) {
 
 int net_fp32_length(int n) {
     if (n < 128 || n > 4096 || n % 16 != 0) return 0;
-    int L = 512;
+    int L = 256;
     while (L < n) L *= 2;
     return L;
 }
@@ -2393,6 +2658,7 @@ cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
         if ((e = cudaGetLastError())) return e;
     }
     switch (len_x(p)) {
+        case 256: return spectra_axis<256>(p, s);
         case 512: return spectra_axis<512>(p, s);
         case 1024: return spectra_axis<1024>(p, s);
         case 2048: return spectra_axis<2048>(p, s);
@@ -2403,6 +2669,7 @@ cudaError_t launch_net_tables(const Plan& p, cudaStream_t s) {
 cudaError_t launch_adjoint_net(const Plan& p, const float* gx, const float* gy, float* gsig, void* work,
                                cudaStream_t s) {
     switch (len_x(p)) {
+        case 256: return run_net_adj_x<256>(p, gx, gy, gsig, work, s);
         case 512: return run_net_adj_x<512>(p, gx, gy, gsig, work, s);
         case 1024: return run_net_adj_x<1024>(p, gx, gy, gsig, work, s);
         case 2048: return run_net_adj_x<2048>(p, gx, gy, gsig, work, s);
@@ -2413,6 +2680,7 @@ cudaError_t launch_adjoint_net(const Plan& p, const float* gx, const float* gy, 
 cudaError_t launch_slab_rows(const Plan& p, const float* sigma_rows, int nrows, void* zr, cudaStream_t s) {
     cf* z = reinterpret_cast<cf*>(zr);
     switch (len_y(p)) {
+        case 256: return slab_rows_l<256>(p, sigma_rows, nrows, z, s);
         case 512: return slab_rows_l<512>(p, sigma_rows, nrows, z, s);
         case 1024: return slab_rows_l<1024>(p, sigma_rows, nrows, z, s);
         case 2048: return slab_rows_l<2048>(p, sigma_rows, nrows, z, s);
@@ -2425,6 +2693,7 @@ cudaError_t launch_slab_cols(const Plan& p, const void* zc, int ky0, int nky, in
     cf* gx = reinterpret_cast<cf*>(gc);
     cf* gy = gx + (size_t)ntiles * p.nx * kGW;
     switch (len_x(p)) {
+        case 256: return slab_cols_l<256>(p, z, ky0, nky, gx, gy, s);
         case 512: return slab_cols_l<512>(p, z, ky0, nky, gx, gy, s);
         case 1024: return slab_cols_l<1024>(p, z, ky0, nky, gx, gy, s);
         case 2048: return slab_cols_l<2048>(p, z, ky0, nky, gx, gy, s);
@@ -2435,6 +2704,7 @@ cudaError_t launch_slab_cols(const Plan& p, const void* zc, int ky0, int nky, in
 cudaError_t launch_slab_rows_inv(const Plan& p, const void* gr, int nrows, float* fx, float* fy, cudaStream_t s) {
     const cf* g = reinterpret_cast<const cf*>(gr);
     switch (len_y(p)) {
+        case 256: return slab_rows_inv_l<256>(p, g, nrows, fx, fy, s);
         case 512: return slab_rows_inv_l<512>(p, g, nrows, fx, fy, s);
         case 1024: return slab_rows_inv_l<1024>(p, g, nrows, fx, fy, s);
         case 2048: return slab_rows_inv_l<2048>(p, g, nrows, fx, fy, s);
@@ -2444,7 +2714,8 @@ cudaError_t launch_slab_rows_inv(const Plan& p, const void* gr, int nrows, float
 
 int net_batch_units(const Plan& p, int pass) {
     if (!net_fp32_eligible(p) || p.prec != TDG_FP32 || len_x(p) > 1024 || len_y(p) > 1024) return 0;
-    const int per_y = len_y(p) == 1024 ? 1 : 2, per_x = len_x(p) == 1024 ? 1 : 2;
+    // lines per unit: one of 1024 points, two of 512, four of 256 (a 64-thread block)
+    const int per_y = 1024 / len_y(p), per_x = 1024 / len_x(p);
     if (pass == 0) return p.nx / per_y;
     if (pass == 1) return (p.hy + per_x - 1) / per_x;
     return 2 * p.nx / per_y;
@@ -2482,6 +2753,7 @@ cudaError_t launch_batched_net(const NetBatchDev& d, int blocks, cudaStream_t s)
 cudaError_t launch_forward_net(const Plan& p, const float* sigma, float* fx, float* fy, void* work,
                                cudaStream_t s) {
     switch (len_x(p)) {
+        case 256: return run_net_x<256>(p, sigma, fx, fy, work, s);
         case 512: return run_net_x<512>(p, sigma, fx, fy, work, s);
         case 1024: return run_net_x<1024>(p, sigma, fx, fy, work, s);
         case 2048: return run_net_x<2048>(p, sigma, fx, fy, work, s);

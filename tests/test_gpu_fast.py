@@ -122,7 +122,7 @@ def test_tc16_adjoint_matches_fp64_gpu():
 
 
 # sides that are multiples of 16 below the transform length (the plan pads to P = 2L,
-# L in {512, 1024, 2048, 4096}; the crop is exact for any P >= 2N - 1)
+# L in {256, 512, 1024, 2048, 4096}; the crop is exact for any P >= 2N - 1)
 @pytest.mark.parametrize("shape,k", [((768, 1024), 3), ((1024, 768), 2), ((512, 384), 1), ((384, 512), 3),
                                      ((128, 160), 3), ((1040, 272), 2), ((3072, 4096), 3), ((144, 2000), 1)])
 def test_padded_network_sizes_vs_fp64_gpu(shape, k):
@@ -132,6 +132,22 @@ def test_padded_network_sizes_vs_fp64_gpu(shape, k):
     f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
     f64 = _forces(nx, ny, k, dx, dy, "fp64", sigma)
     assert rel_l2_pair(*f32, *f64) <= TOL_FP32
+
+
+@pytest.mark.parametrize("shape", [(128, 128), (256, 256), (208, 240), (128, 256), (256, 144)])
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_half_warp_lines_vs_oracle(shape, k):
+    # sides up to 256 run on the 256-point network, two lines per 32-thread block (an odd
+    # number of frequency columns, L + 1: the last block's second half stores nothing)
+    from paper_1904_07400_gb300.api import Plan
+    nx, ny = shape
+    dx, dy = 1.0 / nx, 0.9 / ny
+    assert Plan(nx, ny, k, dx, dy, precision="fp32").path() == 2
+    rng = np.random.default_rng(nx + ny + k)
+    sigma = syn.clumps(nx, ny, seed=nx + 2 * ny) + 0.05 * rng.random((nx, ny))
+    rx, ry = oracle_solver(nx, ny, k, dx, dy).forces(sigma)
+    f32 = _forces(nx, ny, k, dx, dy, "fp32", sigma)
+    assert rel_l2_pair(*f32, rx, ry) <= TOL_FP32
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])

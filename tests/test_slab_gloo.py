@@ -33,7 +33,7 @@ def _setup():
     from paper_1904_07400_gb300 import build, native, slab
     build.build()
     native.load()
-    lx = ly = 512  # the network's transform lengths for 128 and 144 cells
+    lx = ly = 256  # the network's transform lengths for 128 and 144 cells
     px, py = 2 * lx, 2 * ly
     wx, wy = kt.kernel_tables(K, NX, NY, 1.0 / NX, 1.0 / NY)
     return slab, px, py, spectra(wx, wy, px, py)
@@ -95,7 +95,7 @@ def test_partition_covers_rows_and_columns():
     native.load()
     for nx, ny, world in ((128, 144, 2), (4096, 4096, 8), (1040, 272, 3), (256, 4096, 16)):
         parts = slab.partition(nx, ny, world)
-        ly = {272: 512, 144: 512, 4096: 4096}[ny]
+        ly = {272: 512, 144: 256, 4096: 4096}[ny]
         ntile = (ly + 2) // 2
         assert [p[0] for p in parts] == [sum(q[1] for q in parts[:i]) for i in range(world)]
         assert sum(p[1] for p in parts) == nx and all(p[1] % 16 == 0 and p[1] > 0 for p in parts)
