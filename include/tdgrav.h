@@ -155,10 +155,11 @@ tdg_status tdg_batch_create(tdg_batch* out, const tdg_plan* plans, int count,
  * first) or 1 (radix 4).  threads 64: the kernel on the transform network's item bodies
  * (every grid FP32 on the network path with sides up to 1024 cells); the second argument
  * is then the number of units per item (1, 2, 4, 8, 16 or 32; a unit is one row, column or
- * inverse row of a 1024-length transform, or two of a 512-length one): blocks of 64
- * threads take the items of each pass in turn, grouped by the pass's line length and in
- * decreasing solve cost within a group, a 1024-length unit on both warps, a 512-length
- * unit one transform per warp, the column stashes in tensor memory.
+ * inverse row of a 1024-length transform, two of a 512-length one, four of a 256-length
+ * one): blocks of 64 threads take the items of each pass in turn, grouped by the pass's
+ * line length and in decreasing solve cost within a group, a 1024-length unit on both
+ * warps, a 512-length unit one transform per warp, a 256-length unit one per half-warp, the
+ * column stashes in tensor memory.
  * Errors: INVALID_ARG, UNSUPPORTED (a grid does not fit; the old setting stays). */
 tdg_status tdg_batch_set_config(tdg_batch b, int threads, int radix_pref);
 

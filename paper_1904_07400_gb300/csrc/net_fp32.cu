@@ -2036,7 +2036,7 @@ __global__ void __launch_bounds__(kNetBatchThreads, 6) k_batched_net(NetBatchDev
         __syncthreads();
         if (s_ok) {
             // this item's units: idx * U .. (a unit is one transform of a 1024-length line, two
-            // of a 512-length one)
+            // of a 512-length one, four of a 256-length one)
             const int units = phase == 0 ? g.uA : (phase == 1 ? g.uB : g.uC);
             const int u0 = idx * b.units, u1 = min(u0 + b.units, units);
             if (phase == 0) {
