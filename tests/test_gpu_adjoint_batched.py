@@ -44,6 +44,21 @@ def test_adjoint_vs_oracle(shape, k):
         assert _rel(got, ref) <= tol, prec
 
 
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_adjoint_on_half_warp_lines_vs_oracle(k):
+    # sides up to 256 run the adjoint on the 256-point network, two lines per 32-thread
+    # block (columns, then rows with the y solve)
+    nx, ny = 160, 224
+    dx, dy = 1.0 / nx, 1.0 / ny
+    rng = np.random.default_rng(40 + k)
+    gx, gy = rng.standard_normal((nx, ny)), rng.standard_normal((nx, ny))
+    ref = oracle_solver(nx, ny, k, dx, dy).adjoint(gx, gy)
+    p = _plan(nx, ny, k, dx, dy, "fp32")
+    assert p.path() == 2
+    got = to_np(p.adjoint(_t(gx, p), _t(gy, p)))
+    assert _rel(got, ref) <= TOL_FP32
+
+
 def test_adjoint_dot_product_identity_fp64():
     import torch
     N, k = 256, 3
