@@ -18,7 +18,10 @@ and both force components copied back every step.  `forms`: every precision form
 same way, each with its relative L2 error against the FP64 CPU oracle (oracle solves of the
 same grid, timed on all host cores and on one thread, best of 3: `cpu_baseline`).  With
 N > 1 each rank solves its own grid (independent replicas, no collective on the data
-path): weak scaling.
+path): weak scaling.  A one-GPU run also times, after the headline and outside its timed
+region, the method's other workloads (`secondary`: the 256-grid uneven batch as one CUDA
+graph, the adjoint at 2048^2, orders 4 and 5 on the headline grid with their table
+builds); `--no-secondary` skips them.
 """
 from __future__ import annotations
 
@@ -61,6 +64,9 @@ def parse():
                          "radial diagnostics")
     ap.add_argument("--batched", action="store_true",
                     help="time the uneven batch (256 grids, one persistent launch) instead")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workloads that a one-GPU run adds to its line (the 256-grid "
+                         "batch, the 2048^2 adjoint, orders 4 and 5, the kernel-table build)")
     ap.add_argument("--dry-run", action="store_true",
                     help="check the rank launch only: every rank joins a gloo group on the CPU and rank 0 "
                          "prints the world size it saw (no GPU work)")
@@ -491,6 +497,9 @@ def run_ours(args):
     bad = [f for f in forms if results[f]["device_error"]]
     if bad:
         line["device_error"] = bad
+    if rank == 0 and world == 1 and not args.no_secondary and n == N_GRID:
+        del outputs
+        line["secondary"] = secondary_workloads()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -646,6 +655,91 @@ def run_batched(args):
 
 
 E2E_DEPTH = 3
+
+
+def secondary_workloads(steps=20, warmup=3):
+    """The other workloads of the method, timed on the same GPU after the headline (CUDA
+    events, FP32 plans, device-resident synthetic inputs): the 256-grid uneven batch in the
+    autotuner's form replayed as one CUDA graph, the adjoint at 2048^2 (order 3), the forward
+    solve at orders 4 and 5 on the headline grid, and one kernel-table build of it."""
+    import gc
+    import torch
+    from paper_1904_07400_gb300 import autotune
+    from paper_1904_07400_gb300.api import Batch, Plan
+    from workloads import synthetic as syn
+
+    gc.collect()
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    out = {}
+    # the uneven batch
+    specs = syn.batched_specs(256, seed=4)
+    plans, sig = [], []
+    for nx, ny, k, seed in specs:
+        plans.append(Plan(nx, ny, k, 1.0 / nx, 1.0 / ny, precision="fp32"))
+        sig.append(torch.as_tensor(syn.clumps(nx, ny, seed=seed), dtype=torch.float32, device="cuda"))
+    pts = sum(nx * ny for nx, ny, _, _ in specs)
+    b = Batch(plans, sig)
+    tune = autotune.tune(b, None, reps=3)
+    b.launch()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        with torch.cuda.graph(g, stream=s2):
+            b.launch()
+    stream.wait_stream(s2)
+    ms = timed(g.replay)
+    out["batched_256_grids"] = {
+        "ms": round(ms, 4), "Mpts_s": round(pts / (ms * 1e-3) / 1e6, 1), "points": pts,
+        "form": "persistent/%d" % tune["radix_pref"] if tune["mode"] == "persistent" else "streams/%d" % tune["streams"],
+        "candidates_ms": {k: round(v, 4) for k, v in tune["candidates_ms"].items()}, "error": b.error(),
+        "workload": "256 grids, sides from {128,...,1024}, orders 1-3, clumps, seed 4, one CUDA graph"}
+    del b, g, plans, sig
+    gc.collect()
+    torch.cuda.empty_cache()
+    # the adjoint (dL/dsigma for L = sum g_x F^x + g_y F^y) at 2048^2
+    n2 = 2048
+    p = Plan(n2, n2, ORDER, 1.0 / n2, 1.0 / n2, precision="fp32")
+    gx, gy = syn.adjoint_weights(n2, n2, seed=6)
+    tgx = torch.as_tensor(gx, dtype=torch.float32, device="cuda")
+    tgy = torch.as_tensor(gy, dtype=torch.float32, device="cuda")
+    res = torch.empty_like(tgx)
+    ms = timed(lambda: p.adjoint(tgx, tgy, out=res))
+    out["adjoint_2048"] = {"ms": round(ms, 4), "Mpts_s": round(n2 * n2 / (ms * 1e-3) / 1e6, 1),
+                           "error": p.device_error(), "workload": "2048x2048 order 3, g_x, g_y ~ N(0, 1) (seed 6)"}
+    del p, tgx, tgy, res
+    gc.collect()
+    torch.cuda.empty_cache()
+    # orders 4 and 5 on the headline grid, and one table build
+    n = N_GRID
+    sigma = torch.as_tensor(syn.clumps(n, n, seed=SEED), dtype=torch.float32, device="cuda")
+    fx, fy = torch.empty_like(sigma), torch.empty_like(sigma)
+    for k in (4, 5):
+        t0 = time.perf_counter()
+        p = Plan(n, n, k, 1.0 / n, 1.0 / n, precision="fp32")
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        ms = timed(lambda: p.forces(sigma, out=(fx, fy)))
+        out[f"order{k}_{n}"] = {"ms": round(ms, 4), "Mpts_s": round(n * n / (ms * 1e-3) / 1e6, 1),
+                                "table_build_s": round(build_s, 3), "error": p.device_error()}
+        del p
+        gc.collect()
+    return out
 
 
 def run_next2(args):
