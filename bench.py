@@ -258,7 +258,7 @@ class Clocks:
 # still matches, null otherwise.
 MEASURED_TRAFFIC = {
     ("cols_conv", 2, 4096): {"bytes": 268_820_736 + 215_590_912,
-                             "sha256": "03ab72701e4bf29db4b345c77520f5e8bba1ab406d0f3e4b8f9f050d1c704e4a"},
+                             "sha256": "9c3b32e3e86bf85bce6e01d23906a0aefd4b2b0c4725db0bcf5b837c5fa581a5"},
 }
 TRAFFIC_SOURCES = ("paper_1904_07400_gb300/csrc/net_fp32.cu", "paper_1904_07400_gb300/csrc/fft_net.cuh",
                    "paper_1904_07400_gb300/csrc/fft_reg.cuh")

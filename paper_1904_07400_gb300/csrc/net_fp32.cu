@@ -4,13 +4,15 @@
 // (lines of 256 points are half a warp: their kernels run two lines per 32-thread block):
 //
 //  * pass A (rows): chunked register spline solve, packed real transform, unpack, and
-//    16-byte stores of the row's cells into the tiled intermediate Z;
+//    16-byte stores of the row's cells into the tiled intermediate Z (rows of 2048 and
+//    4096 points in pairs: the rows at adjacent positions of Z, sigma by TMA, each tile's
+//    two cells with one 32-byte store);
 //  * pass B (columns): chunked register spline solve, the zero-padded column transform as
 //    two half-length transforms (even and odd frequencies), both spectrum products and
 //    four inverse half-length transforms, with the spectra stored in the network's
 //    output order;
-//  * pass C (rows): TMA bulk-tensor load of one row of G, Hermitian repack, transform,
-//    crop and store.
+//  * pass C (rows): TMA bulk-tensor load of one row of G (of a pair of rows, as 32-byte
+//    pieces, for 2048 and 4096 points), Hermitian repack, transform, crop and store.
 //
 // The padded transforms use the zero padding exactly (no length-2N transform is formed)
 // and the spectra use their parity in kx (half of each half table is stored).
