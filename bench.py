@@ -428,10 +428,17 @@ def oracle_solve(sigma, n, reps=3):
     return f, t_all, t_one, cores
 
 
+def rel_l2_pair(ax, ay, bx, by):
+    """Relative L2 difference of the pair (ax, ay) from (bx, by) over all cells (FP64)."""
+    import numpy as np
+    num = np.sum((np.asarray(ax, np.float64) - bx) ** 2) + np.sum((np.asarray(ay, np.float64) - by) ** 2)
+    den = np.sum(np.asarray(bx, np.float64) ** 2) + np.sum(np.asarray(by, np.float64) ** 2)
+    return float(np.sqrt(num / den))
+
+
 def run_ours(args):
     import numpy as np
     import torch
-    from oracle.norms import rel_l2
     from workloads import synthetic as syn
 
     rank, world, local = dist_setup(args.gpus)
@@ -468,6 +475,9 @@ def run_ours(args):
                         "algorithmic_bytes": algo,
                         "pass_ms": {k: round(v, 4) for k, v in r["per_pass_ms"].items()},
                         "step_bytes": sum(pass_bytes(n, n, r["px"], r["real"], r["path"]).values()),
+                        # sigma in, F^x and F^y out, one quarter spectrum table: 16 B a point (FP32)
+                        "compulsory_bytes": 16 * n * n,
+                        "compulsory_frac": round(16 * n * n / (r["ms"] * 1e-3) / 1e9 / peak, 4),
                         "kernel_path": {0: "generic", 2: "network", 3: "network, tensor-core column pass"}.get(r["path"], "generic")}
     line["e2e"] = {"value": round(world * pts / (r["e2e_ms"] * 1e-3) / 1e6, 1), "unit": "Mpts/s",
                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
@@ -489,11 +499,18 @@ def run_ours(args):
                                           "single_thread_value with numpy pocketfft on one thread; kernel tables "
                                           "built beforehand and not timed"}
         for f in forms:
-            line["forms"][f]["rel_l2_vs_oracle"] = float(f"{rel_l2(*outputs[f], *ref):.3e}")
+            line["forms"][f]["rel_l2_vs_oracle"] = float(f"{rel_l2_pair(*outputs[f], *ref):.3e}")
+        # the 512^2 workload (perturbed D3 disk, seed 2) too, order 3
+        s512 = syn.perturbed_disk(3, 512, seed=2)
+        _, t5_all, t5_one, _ = oracle_solve(s512, 512)
+        line["cpu_baseline"]["config_512"] = {
+            "all_cores_ms": round(t5_all * 1e3, 2), "single_thread_ms": round(t5_one * 1e3, 2),
+            "all_cores_Mpts_s": round(512 * 512 / t5_all / 1e6, 3),
+            "sample": "FP64 oracle solves of the 512x512 perturbed D3 disk (seed 2), order 3, best of 3"}
     if "fp64" in outputs:
         for f in forms:
             if f != "fp64":
-                line["forms"][f]["rel_l2_vs_fp64_gpu"] = float(f"{rel_l2(*outputs[f], *outputs['fp64']):.3e}")
+                line["forms"][f]["rel_l2_vs_fp64_gpu"] = float(f"{rel_l2_pair(*outputs[f], *outputs['fp64']):.3e}")
     bad = [f for f in forms if results[f]["device_error"]]
     if bad:
         line["device_error"] = bad
@@ -659,9 +676,10 @@ E2E_DEPTH = 3
 
 def secondary_workloads(steps=20, warmup=3):
     """The other workloads of the method, timed on the same GPU after the headline (CUDA
-    events, FP32 plans, device-resident synthetic inputs): the 256-grid uneven batch in the
-    autotuner's form replayed as one CUDA graph, the adjoint at 2048^2 (order 3), the forward
-    solve at orders 4 and 5 on the headline grid, and one kernel-table build of it."""
+    events, device-resident synthetic inputs): the 256-grid uneven batch in the autotuner's
+    form replayed as one CUDA graph, the adjoint at 2048^2 (order 3), the 512^2 perturbed
+    disk at orders 1-3 (FP32 against FP64), the forward solve at orders 4 and 5 on the
+    headline grid, and one kernel-table build of it."""
     import gc
     import torch
     from paper_1904_07400_gb300 import autotune
@@ -725,6 +743,26 @@ def secondary_workloads(steps=20, warmup=3):
     del p, tgx, tgy, res
     gc.collect()
     torch.cuda.empty_cache()
+    # the 512^2 workload: perturbed D3 disk (seed 2), orders 1-3, FP32 against FP64 on the GPU
+    n5 = 512
+    s5 = torch.as_tensor(syn.perturbed_disk(3, n5, seed=2), dtype=torch.float64, device="cuda")
+    s5f = s5.float()
+    cfg = {}
+    for k in (1, 2, 3):
+        p32 = Plan(n5, n5, k, 1.0 / n5, 1.0 / n5, precision="fp32")
+        p64 = Plan(n5, n5, k, 1.0 / n5, 1.0 / n5, precision="fp64")
+        o32 = (torch.empty_like(s5f), torch.empty_like(s5f))
+        o64 = (torch.empty_like(s5), torch.empty_like(s5))
+        ms32 = timed(lambda: p32.forces(s5f, out=o32))
+        ms64 = timed(lambda: p64.forces(s5, out=o64))
+        rel = rel_l2_pair(*(o.cpu().numpy() for o in o32), *(o.cpu().numpy() for o in o64))
+        cfg[f"order{k}"] = {"fp32_ms": round(ms32, 4), "fp64_ms": round(ms64, 4),
+                            "fp32_Mpts_s": round(n5 * n5 / (ms32 * 1e-3) / 1e6, 1),
+                            "fp64_Mpts_s": round(n5 * n5 / (ms64 * 1e-3) / 1e6, 1),
+                            "rel_l2_fp32_vs_fp64_gpu": float(f"{rel:.3e}")}
+        del p32, p64
+    out["disk_512"] = cfg
+    gc.collect()
     # orders 4 and 5 on the headline grid, and one table build
     n = N_GRID
     sigma = torch.as_tensor(syn.clumps(n, n, seed=SEED), dtype=torch.float32, device="cuda")
@@ -748,7 +786,6 @@ def run_next2(args):
     and the diagnostics with CUDA events over K calls after W warm-up calls."""
     import numpy as np
     import torch
-    from oracle.analytic import cartesian_force
     from paper_1904_07400_gb300.api import Plan
     from workloads import synthetic as syn
 
@@ -773,10 +810,12 @@ def run_next2(args):
     t_pot_build = time.perf_counter() - t0
     x, y, _, _ = syn.grid(n, n)
     sigma = torch.as_tensor(syn.maclaurin_density(3, x, y, 0.4), dtype=torch.float32, device=dev)
-    X, Y = np.meshgrid(x, y, indexing="ij")
-    ax, _, ar = cartesian_force(3, X, Y, 0.4)
-    ref_x = torch.as_tensor(ax, dtype=torch.float32, device=dev)
-    ref_r = torch.as_tensor(ar, dtype=torch.float32, device=dev)
+    # reference fields for the norms: the FP64 GPU solve of the same disk (its F^x and F_R)
+    p64 = Plan(n, n, k, d, d, precision="fp64", device=dev)
+    gx64, gy64 = p64.forces(sigma.double())
+    ref_x = gx64.float()
+    ref_r = p64.radial_diagnostics(gx64, gy64, -0.5, -0.5)[0].float()
+    del p64
     fx, fy = plan.forces(sigma)
     phi = torch.empty_like(sigma)
     stream = torch.cuda.current_stream(dev)
@@ -809,7 +848,7 @@ def run_next2(args):
             "radial_force_GB_s": round(3 * 4 * n * n / (ms_diag * 1e-3) / 1e9, 1),
             "radial_force_and_norms_ms": round(ms_norms, 4),
             "radial_force_and_norms_GB_s": round(5 * 4 * n * n / (ms_norms * 1e-3) / 1e9, 1),
-            "norms_fx_fr_vs_analytic": [float(f"{v:.4e}") for v in norms],
+            "norms_fx_fr_vs_fp64_gpu": [float(f"{v:.4e}") for v in norms],
             "device_error": plan.device_error()}
     print(json.dumps(line), flush=True)
 
