@@ -71,13 +71,13 @@ def test_init_validates_arguments(lib):
         assert st == 1 and not h.value, args
     st, _ = _init(lib, 4097, 64, 3, 0.1, 0.1, 1.0, 1, 0)
     assert st == 2
-    # the tensor-core form exists for sides of 1024, 2048 and 4096 cells only
+    # the tensor-core form needs columns padded to 2048 or 4096 points (nx > 1024)
     st, h = _init(lib, 512, 512, 3, 0.1, 0.1, 1.0, 2, 0)
     assert st == 2 and not h.value
     st, h = _init(lib, 4096, 1024, 3, 0.1, 0.1, 1.0, 2, 0)
     assert st == 0
     lib.tdg_destroy(h)
-    # orders 4 and 5 run the FP64 and FP32 forms; the tensor-core form is order 1-3 only
+    # orders 4 and 5 run every form; the tensor-core form still needs nx > 1024
     for k in (4, 5):
         for prec in (0, 1):
             st, h = _init(lib, 64, 48, k, 0.1, 0.1, 1.0, prec, 0)
@@ -86,6 +86,25 @@ def test_init_validates_arguments(lib):
         st, h = _init(lib, 1024, 1024, k, 0.1, 0.1, 1.0, 2, 0)
         assert st == 2 and not h.value
     assert lib.tdg_init(None, 64, 64, 3, 0.1, 0.1, 1.0, 1, 0) == 1
+
+
+@pytest.mark.parametrize("n,period", [(128, 512), (144, 512), (256, 512), (272, 1024), (512, 1024), (528, 2048),
+                                      (1024, 2048), (1040, 4096), (2064, 8192), (4096, 8192)])
+def test_network_period_choice(lib, n, period):
+    # FP32 sides that are multiples of 16 from 128 to 4096 pad to 2L, L the smallest
+    # transform-network length (256, 512, 1024, 2048, 4096) not below the side; FP64
+    # plans of the same sides keep the smallest even 2^a 3^b >= 2n - 1
+    st, h = _init(lib, n, n, 3, 0.1, 0.1, 1.0, 1, 0)
+    assert st == 0
+    px, py = ctypes.c_int(), ctypes.c_int()
+    lib.tdg_plan_info(h, ctypes.byref(px), ctypes.byref(py), None, None)
+    assert (px.value, py.value) == (period, period)
+    lib.tdg_destroy(h)
+    st, h = _init(lib, n, n, 3, 0.1, 0.1, 1.0, 0, 0)
+    lib.tdg_plan_info(h, ctypes.byref(px), None, None, None)
+    p = px.value
+    assert p >= 2 * n - 1 and p % 2 == 0 and p <= period
+    lib.tdg_destroy(h)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 17, 33, 64, 100, 192, 4096])
